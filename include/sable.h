@@ -1,0 +1,185 @@
+/*
+ * sable.h -- C ABI of the GB300 hybrid VDIA+VBR+CSR SpMV/SpMM library.
+ *
+ * The library follows the plan -> extract -> dispatch pipeline of the paper
+ * (Section 3, Fig. 2): a plan holds a sparse matrix and an ordered list of
+ * extractors; extraction carves the matrix into VDIA diagonal segments
+ * (Section 4.2, Algorithms 3 and 4), VBR dense blocks (Section 4.1,
+ * Algorithms 1 and 2) and a CSR remainder (Appendix A.1); the SpMV/SpMM
+ * entry points then compute y = A x or C = A B (Section 5, "Kernels") with one
+ * CUDA kernel launch over a device table of row tiles.  Extraction runs on the
+ * host (native C++); every arithmetic step of SpMV/SpMM runs in this
+ * library's CUDA kernels.  There is no CPU fallback: without a CUDA device the
+ * compute calls return SABLE_ERR_CUDA.
+ *
+ * Conventions for every call:
+ *   - Indices are 0-based.  Matrices are m x n.  Dense operands are row-major.
+ *   - Host pointers are read during the call only and copied where kept.
+ *   - Device pointers (x, y, B, C, the pointer tables of the batch calls) are
+ *     owned by the caller and must stay valid until the stream work ends.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); compute
+ *     calls are asynchronous and ordered on it.
+ *   - Errors are reported by status code only; the library never aborts or
+ *     prints.  The first error of a plan is kept (sticky) and returned by
+ *     every later call on that plan; sable_plan_status() reads it.
+ *   - A plan may be used by one host thread at a time.
+ */
+#ifndef SABLE_H
+#define SABLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SABLE_OK = 0,
+  SABLE_ERR_INVALID = 1,     /* bad argument: index out of range, size, NULL   */
+  SABLE_ERR_OOM = 2,         /* host or device allocation failed               */
+  SABLE_ERR_CUDA = 3,        /* a CUDA runtime call failed (or no device)      */
+  SABLE_ERR_INCOMPLETE = 4,  /* extractors left entries unclaimed (Section 3)  */
+  SABLE_ERR_ORDER = 5,       /* call made in the wrong phase of the plan       */
+  SABLE_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                  */
+  SABLE_ERR_KERNEL = 7,      /* a kernel's own bounds check tripped            */
+  SABLE_ERR_UNSUPPORTED = 8  /* valid request this build does not implement    */
+} sable_status;
+
+/* Extractor kinds (Section 3.2).  SABLE_X_CSR claims everything left and must
+ * come last for the plan to be complete. */
+typedef enum { SABLE_X_VDIA = 0, SABLE_X_VBR = 1, SABLE_X_CSR = 2 } sable_extractor;
+
+/* Arithmetic of the VBR blocks in SpMM.  SABLE_BF16_BLOCKS stores each block
+ * as bfloat16 (round to nearest even) of value / s_b with a per-block power of
+ * two s_b = 2^ceil(log2 max|a|), rounds the B rows it multiplies to bfloat16,
+ * runs the block products on the tensor cores (tcgen05, FP32 accumulation)
+ * and multiplies by s_b; VDIA and CSR parts stay FP32. */
+typedef enum { SABLE_FP32 = 0, SABLE_BF16_BLOCKS = 1 } sable_precision;
+
+/* Extractor parameters.  Fields an extractor does not use are ignored.
+ *   delta        density floor (Section 4.1: 0.5 for blocks; Section 5 uses
+ *                0.75 for bands)
+ *   a_min        minimum area of a block / of a band candidate (2500)
+ *   l_seg        minimum rows of a VDIA segment (Algorithm 4)
+ *   w_max        largest ribbon half-width FitRibbon may reach
+ *   d_max        largest |diagonal offset| considered (0 = all)
+ *   count_min    entries a diagonal needs to be a candidate (0 = ceil(delta*l_seg))
+ *   coverage_min share of entries blocks must cover, else none are kept (0.08)
+ *   max_span     cap on FindBlock's outer span (Algorithm 2)
+ *   tile         candidate-region pre-pass cell size; 0 runs Algorithm 1 on
+ *                the whole matrix */
+typedef struct {
+  double delta;
+  int64_t a_min;
+  int32_t l_seg;
+  int32_t w_max;
+  int64_t d_max;
+  int64_t count_min;
+  double coverage_min;
+  int32_t max_span;
+  int32_t tile;
+} sable_extract_params;
+
+/* Summary of an extracted plan.  Byte counts are the algorithmic bytes one
+ * call must move: every stored value, index and pointer once, x (or B) once
+ * and y (or C) written once. */
+typedef struct {
+  int64_t m, n, nnz;                 /* canonical entries (duplicates summed)  */
+  int64_t nnz_vdia, nnz_vbr, nnz_csr;/* entries claimed by each format         */
+  int64_t n_segments, n_diagonals;   /* VDIA segments, sum of their diagonals  */
+  int64_t vdia_cells;                /* stored VDIA cells (entries + padding)  */
+  int64_t n_blocks, vbr_cells;       /* VBR blocks and their stored cells      */
+  int64_t n_items;                   /* row tiles of the SpMV launch           */
+  int64_t spmv_bytes;                /* algorithmic bytes of one sable_spmv    */
+  int64_t csr_spmv_bytes;            /* same for plain CSR of the whole matrix */
+} sable_plan_stats;
+
+typedef struct sable_plan_s *sable_plan_t;
+typedef struct sable_batch_s *sable_batch_t;
+
+/* Fill `out` with the defaults for one extractor kind. */
+void sable_default_params(sable_extractor kind, sable_extract_params *out);
+
+/* Create a plan from host COO triples (copied).  nnz may be 0.  Duplicate
+ * coordinates are summed (FP64 in input order, rounded once to FP32);
+ * explicit zeros are structural entries.  Errors: SABLE_ERR_INVALID for a
+ * negative size, m or n >= 2^31, nnz >= 2^31, a NULL array with nnz > 0 or
+ * an index outside the matrix; SABLE_ERR_OOM. */
+sable_status sable_plan_create(int64_t m, int64_t n, int64_t nnz, const int32_t *row,
+                               const int32_t *col, const float *val, sable_plan_t *out);
+
+/* Append an extractor (Section 3, "Extract").  params NULL = defaults.
+ * Errors: SABLE_ERR_ORDER after sable_extract; SABLE_ERR_INVALID. */
+sable_status sable_plan_add_extractor(sable_plan_t plan, sable_extractor kind,
+                                      const sable_extract_params *params);
+
+/* Run the extractors in order over the residual, check that the residual is
+ * empty and that the regions partition the entries exactly, and build the
+ * host tables (Section 3, "Extract"/"Dispatch", Section 3.4).  Host only: no
+ * CUDA call.  Errors: SABLE_ERR_INCOMPLETE if entries are left unclaimed;
+ * SABLE_ERR_ORDER if called twice. */
+sable_status sable_extract(sable_plan_t plan);
+
+/* Copy the plan's tables to the current CUDA device (asynchronously on
+ * `stream`; host copies are kept until destroy).  Errors: SABLE_ERR_ORDER
+ * before sable_extract; SABLE_ERR_OOM / SABLE_ERR_CUDA. */
+sable_status sable_plan_upload(sable_plan_t plan, void *stream);
+
+/* y := A x.  x: device, n floats; y: device, m floats (overwritten).
+ * Errors: SABLE_ERR_ORDER before upload; SABLE_ERR_INVALID; SABLE_ERR_CUDA. */
+sable_status sable_spmv(sable_plan_t plan, const float *x, float *y, void *stream);
+
+/* C := A B.  B: device, n x N row-major with leading dimension ldb >= N;
+ * C: device, m x N row-major, ldc >= N (overwritten).  N >= 1.
+ * SABLE_BF16_BLOCKS as documented at sable_precision. */
+sable_status sable_spmm(sable_plan_t plan, const float *B, int64_t N, int64_t ldb, float *C,
+                        int64_t ldc, sable_precision prec, void *stream);
+
+/* Plain CSR SpMV of the whole canonical matrix (no extraction), with the
+ * library's CSR kernel: the "plain GPU CSR" comparison point.  Requires
+ * upload.  y := A x as for sable_spmv. */
+sable_status sable_csr_spmv(sable_plan_t plan, const float *x, float *y, void *stream);
+
+/* Plain CSR SpMM of the whole canonical matrix (comparison point). */
+sable_status sable_csr_spmm(sable_plan_t plan, const float *B, int64_t N, int64_t ldb,
+                            float *C, int64_t ldc, void *stream);
+
+/* Statistics of an extracted plan.  Errors: SABLE_ERR_ORDER before extract. */
+sable_status sable_plan_info(sable_plan_t plan, sable_plan_stats *out);
+
+/* Host exports of an extracted plan (for checking; sizes from plan_info).
+ * segments: n_segments x 4 int64 (row_start, nrows, lowest offset, ndiags),
+ *           sorted by row_start; diagonals of a segment are consecutive
+ *           offsets.
+ * blocks:   n_blocks x 4 int64 (row0, nrows, col0, ncols), sorted by row0.
+ * vdia values: vdia_cells floats, segment by segment, diagonal-major
+ *           (Fig. 4 layout, no padding).
+ * vbr values: vbr_cells floats, block by block, column-major (Fig. 7).
+ * csr: row_ptr m+1 int64, col nnz_csr int32, val nnz_csr floats, rows sorted,
+ *           columns ascending within a row. */
+sable_status sable_plan_get_segments(sable_plan_t plan, int64_t *out);
+sable_status sable_plan_get_blocks(sable_plan_t plan, int64_t *out);
+sable_status sable_plan_get_vdia_values(sable_plan_t plan, float *out);
+sable_status sable_plan_get_vbr_values(sable_plan_t plan, float *out);
+sable_status sable_plan_get_csr(sable_plan_t plan, int64_t *row_ptr, int32_t *col, float *val);
+
+/* Tuning of the row tiles ("items") one launch works on.  rows_per_item is a
+ * multiple of 4 in [4, 1024]; item_bytes is the target algorithmic bytes per
+ * tile; threads is 128, 256 or 512.  Takes effect at the next upload.
+ * Errors: SABLE_ERR_INVALID. */
+sable_status sable_plan_set_tiling(sable_plan_t plan, int32_t rows_per_item, int64_t item_bytes,
+                                   int32_t threads);
+
+/* First error recorded on the plan (SABLE_OK if none). */
+sable_status sable_plan_status(sable_plan_t plan);
+
+/* Free host and device memory of the plan.  NULL is accepted. */
+sable_status sable_plan_destroy(sable_plan_t plan);
+
+/* Static description of a status code. */
+const char *sable_status_string(sable_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SABLE_H */

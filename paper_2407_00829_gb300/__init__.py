@@ -1,0 +1,249 @@
+"""Python binding of libsable (include/sable.h): argument marshalling only.
+
+Every SpMV/SpMM step runs in the library's CUDA kernels; PyTorch supplies
+device memory and streams.  Loading fails loudly when the library is missing
+(there is no CPU fallback): build it with ``paper_2407_00829_gb300.build.build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsable.so")
+
+VDIA, VBR, CSR = 0, 1, 2
+FP32, BF16_BLOCKS = 0, 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime error",
+          4: "incomplete plan", 5: "call out of order", 6: "device wait timed out",
+          7: "kernel bounds check failed", 8: "unsupported"}
+
+EXPORTED = [
+    "sable_default_params", "sable_plan_create", "sable_plan_add_extractor", "sable_extract",
+    "sable_plan_upload", "sable_spmv", "sable_spmm", "sable_csr_spmv", "sable_csr_spmm",
+    "sable_plan_info", "sable_plan_get_segments", "sable_plan_get_blocks",
+    "sable_plan_get_vdia_values", "sable_plan_get_vbr_values", "sable_plan_get_csr",
+    "sable_plan_set_tiling", "sable_plan_status", "sable_plan_destroy", "sable_status_string",
+]
+
+
+class SableError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({status})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("a_min", ctypes.c_int64), ("l_seg", ctypes.c_int32),
+                ("w_max", ctypes.c_int32), ("d_max", ctypes.c_int64), ("count_min", ctypes.c_int64),
+                ("coverage_min", ctypes.c_double), ("max_span", ctypes.c_int32),
+                ("tile", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "m", "n", "nnz", "nnz_vdia", "nnz_vbr", "nnz_csr", "n_segments", "n_diagonals",
+        "vdia_cells", "n_blocks", "vbr_cells", "n_items", "spmv_bytes", "csr_spmv_bytes")]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsable.so (built in-tree).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsable.so not built ({LIB_PATH}); run "
+                               "paper_2407_00829_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        p, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        sig = {
+            "sable_default_params": ([i32, p], None),
+            "sable_plan_create": ([i64, i64, i64, p, p, p, p], i32),
+            "sable_plan_add_extractor": ([p, i32, p], i32),
+            "sable_extract": ([p], i32),
+            "sable_plan_upload": ([p, p], i32),
+            "sable_spmv": ([p, p, p, p], i32),
+            "sable_csr_spmv": ([p, p, p, p], i32),
+            "sable_spmm": ([p, p, i64, i64, p, i64, i32, p], i32),
+            "sable_csr_spmm": ([p, p, i64, i64, p, i64, p], i32),
+            "sable_plan_info": ([p, p], i32),
+            "sable_plan_get_segments": ([p, p], i32),
+            "sable_plan_get_blocks": ([p, p], i32),
+            "sable_plan_get_vdia_values": ([p, p], i32),
+            "sable_plan_get_vbr_values": ([p, p], i32),
+            "sable_plan_get_csr": ([p, p, p, p], i32),
+            "sable_plan_set_tiling": ([p, i32, i64, i32], i32),
+            "sable_plan_status": ([p], i32),
+            "sable_plan_destroy": ([p], i32),
+            "sable_status_string": ([i32], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise SableError(st, what)
+
+
+def default_params(kind: int) -> Params:
+    p = Params()
+    lib().sable_default_params(kind, ctypes.byref(p))
+    return p
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t) -> int:
+    return t.data_ptr()
+
+
+class Plan:
+    """A matrix, its ordered extractors and, after ``extract``/``upload``, its
+    hybrid VDIA+VBR+CSR form on the host and the device."""
+
+    def __init__(self, m: int, n: int, row, col, val):
+        row = np.ascontiguousarray(row, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float32)
+        if not (row.shape == col.shape == val.shape):
+            raise ValueError("COO arrays differ in length")
+        h = ctypes.c_void_p()
+        _check(lib().sable_plan_create(int(m), int(n), int(val.size), row.ctypes.data,
+                                       col.ctypes.data, val.ctypes.data, ctypes.byref(h)),
+               "sable_plan_create")
+        self._h = h
+        self.m, self.n = int(m), int(n)
+
+    # -- life cycle
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sable_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def add_extractor(self, kind: int, params: Optional[Params] = None, **kw):
+        p = params if params is not None else default_params(kind)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        _check(lib().sable_plan_add_extractor(self._h, kind, ctypes.byref(p)), "add_extractor")
+        return self
+
+    def extract(self):
+        _check(lib().sable_extract(self._h), "sable_extract")
+        return self
+
+    def set_tiling(self, rows_per_item=512, item_bytes=48 * 1024, threads=256):
+        _check(lib().sable_plan_set_tiling(self._h, rows_per_item, item_bytes, threads), "set_tiling")
+        return self
+
+    def upload(self, stream=None):
+        _check(lib().sable_plan_upload(self._h, _stream_handle(stream)), "sable_plan_upload")
+        return self
+
+    # -- compute (device tensors)
+    def spmv(self, x, y, stream=None):
+        _check(lib().sable_spmv(self._h, _dptr(x), _dptr(y), _stream_handle(stream)), "sable_spmv")
+        return y
+
+    def csr_spmv(self, x, y, stream=None):
+        _check(lib().sable_csr_spmv(self._h, _dptr(x), _dptr(y), _stream_handle(stream)), "sable_csr_spmv")
+        return y
+
+    def spmm(self, B, C, precision: int = FP32, stream=None):
+        N = B.shape[1]
+        _check(lib().sable_spmm(self._h, _dptr(B), N, B.stride(0), _dptr(C), C.stride(0), precision,
+                                _stream_handle(stream)), "sable_spmm")
+        return C
+
+    def csr_spmm(self, B, C, stream=None):
+        N = B.shape[1]
+        _check(lib().sable_csr_spmm(self._h, _dptr(B), N, B.stride(0), _dptr(C), C.stride(0),
+                                    _stream_handle(stream)), "sable_csr_spmm")
+        return C
+
+    # -- host views
+    def info(self) -> dict:
+        s = Stats()
+        _check(lib().sable_plan_info(self._h, ctypes.byref(s)), "sable_plan_info")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def segments(self) -> np.ndarray:
+        k = self.info()["n_segments"]
+        out = np.zeros((k, 4), dtype=np.int64)
+        _check(lib().sable_plan_get_segments(self._h, out.ctypes.data), "get_segments")
+        return out
+
+    def blocks(self) -> np.ndarray:
+        k = self.info()["n_blocks"]
+        out = np.zeros((k, 4), dtype=np.int64)
+        _check(lib().sable_plan_get_blocks(self._h, out.ctypes.data), "get_blocks")
+        return out
+
+    def vdia_values(self) -> np.ndarray:
+        out = np.zeros(self.info()["vdia_cells"], dtype=np.float32)
+        _check(lib().sable_plan_get_vdia_values(self._h, out.ctypes.data), "get_vdia_values")
+        return out
+
+    def vbr_values(self) -> np.ndarray:
+        out = np.zeros(self.info()["vbr_cells"], dtype=np.float32)
+        _check(lib().sable_plan_get_vbr_values(self._h, out.ctypes.data), "get_vbr_values")
+        return out
+
+    def csr(self):
+        k = self.info()["nnz_csr"]
+        rp = np.zeros(self.m + 1, dtype=np.int64)
+        ci = np.zeros(max(k, 1), dtype=np.int32)
+        cv = np.zeros(max(k, 1), dtype=np.float32)
+        _check(lib().sable_plan_get_csr(self._h, rp.ctypes.data, ci.ctypes.data, cv.ctypes.data), "get_csr")
+        return rp, ci[:k], cv[:k]
+
+    def status(self) -> int:
+        return lib().sable_plan_status(self._h)
+
+
+def plan_from(A: dict, extractors, tiling: Optional[dict] = None, upload: bool = True, stream=None) -> Plan:
+    """Create, extract and (optionally) upload a plan for a COO dict
+    {m, n, row, col, val}; ``extractors`` is a list of (kind, params-dict or None)."""
+    P = Plan(A["m"], A["n"], A["row"], A["col"], A["val"])
+    for kind, kw in extractors:
+        P.add_extractor(kind, **(kw or {}))
+    P.extract()
+    if tiling:
+        P.set_tiling(**tiling)
+    if upload:
+        P.upload(stream)
+    return P

@@ -1,0 +1,171 @@
+// Band extractor: Appendix D, Algorithm 3 (ExtractBands) and Algorithm 4
+// (GrowSegments), with the FitRibbon step that Section 4.2 names but does not
+// define.  Host C++, threaded over rows where rows are independent.
+//
+// Readings (identical to the library's documented behaviour):
+//  * M[d] counts residual entries on diagonal d = j - i, |d| <= d_max.
+//    Candidates: M[d] >= count_min, by decreasing M[d], ties by increasing d.
+//  * FitRibbon(i, d): (0,0,0) unless row i holds an entry at column i + d.
+//    Otherwise the ribbon grows from that cell; each step reaches the nearest
+//    entry below or above the ribbon (adding one entry and the zeros between),
+//    takes the narrower result (below on a tie) if its density stays >= delta
+//    and the side's extent stays <= w_max, and stops otherwise.  k_i = entries
+//    in the final ribbon.
+//  * GrowSegments as printed: rolling maximum (L, U); a widened extent recounts
+//    the whole segment, an unchanged one adds row j's entries inside the
+//    ribbon; the segment ends when its density drops below delta; segments
+//    shorter than l_seg rows are dropped.
+//  * A candidate is accepted when the summed area of its segments is >= a_min
+//    and their density is >= delta; accepted rows are masked for later
+//    candidates.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <thread>
+#include <unordered_map>
+
+#include "sable_internal.h"
+
+namespace sable {
+
+int64_t Csr::count(int64_t i, int64_t lo, int64_t hi) const {
+  if (hi < lo) return 0;
+  const int32_t *b = ci.data() + rp[i], *e = ci.data() + rp[i + 1];
+  const int32_t *a = std::lower_bound(b, e, (int32_t)std::max<int64_t>(lo, INT32_MIN));
+  const int32_t *z = std::upper_bound(a, e, (int32_t)std::min<int64_t>(hi, INT32_MAX));
+  return z - a;
+}
+
+template <class F>
+static void parallel_rows(int64_t n, F &&f) {
+  const int T = host_threads();
+  if (T <= 1 || n < 4096) {
+    f(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  const int64_t chunk = (n + T - 1) / T;
+  for (int t = 0; t < T; ++t) {
+    int64_t a = t * chunk, b = std::min(n, a + chunk);
+    if (a >= b) break;
+    th.emplace_back([&, a, b] { f(a, b); });
+  }
+  for (auto &x : th) x.join();
+}
+
+struct Ext { int32_t l, u, k; };
+
+static Ext fit_ribbon(const Csr &R, int64_t i, int64_t d, double delta, int64_t w_max) {
+  const int64_t c = i + d;
+  if (c < 0 || c >= R.n) return {0, 0, 0};
+  const int32_t *b = R.ci.data() + R.rp[i], *e = R.ci.data() + R.rp[i + 1];
+  const int32_t *p = std::lower_bound(b, e, (int32_t)c);
+  if (p == e || *p != c) return {0, 0, 0};
+  const int64_t len = e - b;
+  int64_t lo = p - b, hi = lo, l = 0, u = 0, z = 1;
+  for (;;) {
+    int64_t wb = -1, wa = -1, nl = 0, nu = 0;
+    if (lo > 0 && c - b[lo - 1] <= w_max) {
+      nl = c - b[lo - 1];
+      wb = nl + u + 1;
+    }
+    if (hi + 1 < len && b[hi + 1] - c <= w_max) {
+      nu = b[hi + 1] - c;
+      wa = l + nu + 1;
+    }
+    if (wb < 0 && wa < 0) break;
+    const bool below = wb >= 0 && (wa < 0 || wb <= wa);
+    const int64_t w = below ? wb : wa;
+    if ((double)(z + 1) / (double)w < delta) break;
+    ++z;
+    if (below) {
+      l = nl;
+      --lo;
+    } else {
+      u = nu;
+      ++hi;
+    }
+  }
+  return {(int32_t)l, (int32_t)u, (int32_t)z};
+}
+
+// Entries of row r whose offset (col - r) lies in [olo, ohi].
+static inline int64_t ribbon_count(const Csr &R, int64_t r, int64_t olo, int64_t ohi) {
+  return R.count(r, r + olo, r + ohi);
+}
+
+std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p) {
+  const int64_t m = R.m, n = R.n;
+  const int64_t d_max = p.d_max > 0 ? p.d_max : std::max(m, n);
+  const int64_t count_min =
+      p.count_min > 0 ? p.count_min : (int64_t)std::ceil(p.delta * (double)p.l_seg);
+  // M[d] over the offset range [-(m-1), n-1]
+  const int64_t span = m + n;
+  std::vector<int64_t> M(span > 0 ? span : 1, 0);
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t k = R.rp[i]; k < R.rp[i + 1]; ++k) {
+      const int64_t d = (int64_t)R.ci[k] - i;
+      if (d <= d_max && -d <= d_max) ++M[d + m];
+    }
+  std::vector<int64_t> D;
+  for (int64_t t = 0; t < span; ++t)
+    if (M[t] > 0 && M[t] >= count_min) D.push_back(t - m);
+  std::stable_sort(D.begin(), D.end(), [&](int64_t a, int64_t b) {
+    if (M[a + m] != M[b + m]) return M[a + m] > M[b + m];
+    return a < b;
+  });
+
+  std::vector<uint8_t> used(m, 0);
+  std::vector<Ext> ext(m);
+  std::vector<BandSeg> out;
+  for (const int64_t d : D) {
+    parallel_rows(m, [&](int64_t a, int64_t b) {
+      for (int64_t i = a; i < b; ++i)
+        ext[i] = used[i] ? Ext{0, 0, 0} : fit_ribbon(R, i, d, p.delta, p.w_max);
+    });
+    // GrowSegments (Algorithm 4)
+    std::vector<BandSeg> S;
+    int64_t i = 0;
+    while (i < m) {
+      if (ext[i].k == 0) {
+        ++i;
+        continue;
+      }
+      const int64_t i0 = i;
+      int64_t L = ext[i].l, U = ext[i].u;
+      int64_t z = ribbon_count(R, i0, d - L, d + U);
+      int64_t j = i + 1;
+      while (j < m && ext[j].k > 0) {
+        const int64_t L2 = std::max<int64_t>(L, ext[j].l), U2 = std::max<int64_t>(U, ext[j].u);
+        int64_t z2;
+        if (L2 != L || U2 != U) {
+          z2 = 0;
+          for (int64_t r = i0; r <= j; ++r) z2 += ribbon_count(R, r, d - L2, d + U2);
+        } else {
+          z2 = z + ribbon_count(R, j, d - L, d + U);
+        }
+        if ((double)z2 / (double)((L2 + U2 + 1) * (j - i0 + 1)) < p.delta) break;
+        L = L2;
+        U = U2;
+        z = z2;
+        ++j;
+      }
+      if (j - i0 >= p.l_seg) S.push_back({i0, j, d, L, U, z});
+      i = j;
+    }
+    if (S.empty()) continue;
+    int64_t area = 0, zz = 0;
+    for (auto &s : S) {
+      area += (s.L + s.U + 1) * (s.i1 - s.i0);
+      zz += s.z;
+    }
+    if (area < p.a_min || (double)zz / (double)area < p.delta) continue;
+    for (auto &s : S) {
+      for (int64_t r = s.i0; r < s.i1; ++r) used[r] = 1;
+      out.push_back(s);
+    }
+  }
+  return out;
+}
+
+}  // namespace sable

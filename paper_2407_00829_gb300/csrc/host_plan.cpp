@@ -1,0 +1,347 @@
+// Plan life cycle on the host: COO ingest and canonical form, the ordered
+// extractor list, extraction over the shrinking residual (Section 3,
+// "Initialize" / "Extract"), the completeness check (Section 3, "Dispatch"),
+// and host exports.  No CUDA call is made here.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "sable_internal.h"
+
+using namespace sable;
+
+namespace sable {
+
+sable_status fail(sable_plan_t p, sable_status s) {
+  if (p && p->sticky == SABLE_OK) p->sticky = s;
+  return s;
+}
+
+// Residual (owner < 0) of the canonical matrix as CSR, or its transpose.
+static Csr residual(const sable_plan_s &P, bool transpose) {
+  Csr R;
+  R.m = transpose ? P.n : P.m;
+  R.n = transpose ? P.m : P.n;
+  R.rp.assign(R.m + 1, 0);
+  const Csr &C = P.canon;
+  for (int64_t i = 0; i < C.m; ++i)
+    for (int64_t k = C.rp[i]; k < C.rp[i + 1]; ++k)
+      if (P.owner[k] < 0) ++R.rp[(transpose ? C.ci[k] : i) + 1];
+  for (int64_t i = 0; i < R.m; ++i) R.rp[i + 1] += R.rp[i];
+  R.ci.resize(R.rp[R.m]);
+  R.id.resize(R.rp[R.m]);
+  std::vector<int64_t> pos(R.rp.begin(), R.rp.end() - 1);
+  for (int64_t i = 0; i < C.m; ++i)   // row-major sweep keeps inner indices sorted
+    for (int64_t k = C.rp[i]; k < C.rp[i + 1]; ++k) {
+      if (P.owner[k] >= 0) continue;
+      const int64_t o = transpose ? C.ci[k] : i;
+      const int64_t q = pos[o]++;
+      R.ci[q] = transpose ? (int32_t)i : C.ci[k];
+      R.id[q] = k;
+    }
+  return R;
+}
+
+}  // namespace sable
+
+extern "C" {
+
+const char *sable_status_string(sable_status s) {
+  switch (s) {
+    case SABLE_OK: return "ok";
+    case SABLE_ERR_INVALID: return "invalid argument";
+    case SABLE_ERR_OOM: return "out of memory";
+    case SABLE_ERR_CUDA: return "CUDA runtime error";
+    case SABLE_ERR_INCOMPLETE: return "incomplete plan: entries left unclaimed";
+    case SABLE_ERR_ORDER: return "call out of order for this plan";
+    case SABLE_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SABLE_ERR_KERNEL: return "kernel bounds check failed";
+    case SABLE_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+void sable_default_params(sable_extractor kind, sable_extract_params *o) {
+  if (!o) return;
+  o->delta = kind == SABLE_X_VDIA ? 0.75 : 0.5;
+  o->a_min = 2500;
+  o->l_seg = 32;
+  o->w_max = 64;
+  o->d_max = 0;
+  o->count_min = 0;
+  o->coverage_min = 0.08;
+  o->max_span = 512;
+  o->tile = 8;
+}
+
+sable_status sable_plan_create(int64_t m, int64_t n, int64_t nnz, const int32_t *row,
+                               const int32_t *col, const float *val, sable_plan_t *out) {
+  if (!out) return SABLE_ERR_INVALID;
+  *out = nullptr;
+  if (m < 0 || n < 0 || nnz < 0 || m >= INT32_MAX || n >= INT32_MAX || nnz >= INT32_MAX)
+    return SABLE_ERR_INVALID;
+  if (nnz > 0 && (!row || !col || !val)) return SABLE_ERR_INVALID;
+  for (int64_t k = 0; k < nnz; ++k)
+    if (row[k] < 0 || row[k] >= m || col[k] < 0 || col[k] >= n) return SABLE_ERR_INVALID;
+  sable_plan_s *P = new (std::nothrow) sable_plan_s();
+  if (!P) return SABLE_ERR_OOM;
+  try {
+    P->m = m;
+    P->n = n;
+    // bucket by row, keeping input order, then order each row by column
+    std::vector<int64_t> cnt(m + 1, 0);
+    for (int64_t k = 0; k < nnz; ++k) ++cnt[row[k] + 1];
+    for (int64_t i = 0; i < m; ++i) cnt[i + 1] += cnt[i];
+    std::vector<int64_t> order(nnz);
+    {
+      std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+      for (int64_t k = 0; k < nnz; ++k) order[pos[row[k]]++] = k;
+    }
+    Csr &C = P->canon;
+    C.m = m;
+    C.n = n;
+    C.rp.assign(m + 1, 0);
+    C.ci.reserve(nnz);
+    P->cval.reserve(nnz);
+    for (int64_t i = 0; i < m; ++i) {
+      int64_t *b = order.data() + cnt[i], *e = order.data() + cnt[i + 1];
+      std::stable_sort(b, e, [&](int64_t a, int64_t z) { return col[a] < col[z]; });
+      for (int64_t *q = b; q < e;) {
+        const int32_t c = col[*q];
+        double s = 0.0;
+        for (; q < e && col[*q] == c; ++q) s += (double)val[*q];   // input order
+        C.ci.push_back(c);
+        P->cval.push_back((float)s);
+      }
+      C.rp[i + 1] = (int64_t)C.ci.size();
+    }
+    C.id.clear();
+    P->owner.assign(C.ci.size(), OWN_NONE);
+  } catch (const std::bad_alloc &) {
+    delete P;
+    return SABLE_ERR_OOM;
+  }
+  *out = P;
+  return SABLE_OK;
+}
+
+sable_status sable_plan_add_extractor(sable_plan_t P, sable_extractor kind,
+                                      const sable_extract_params *params) {
+  if (!P) return SABLE_ERR_INVALID;
+  if (P->sticky) return P->sticky;
+  if (P->extracted) return SABLE_ERR_ORDER;
+  if (kind != SABLE_X_VDIA && kind != SABLE_X_VBR && kind != SABLE_X_CSR) return SABLE_ERR_INVALID;
+  sable_extract_params p;
+  sable_default_params(kind, &p);
+  if (params) p = *params;
+  if (!(p.delta > 0.0 && p.delta <= 1.0) || p.a_min < 1 || p.l_seg < 1 || p.w_max < 0 ||
+      p.d_max < 0 || p.count_min < 0 || !(p.coverage_min >= 0.0) || p.max_span < 1 ||
+      p.tile < 0)
+    return SABLE_ERR_INVALID;
+  P->extractors.push_back({kind, p});
+  return SABLE_OK;
+}
+
+sable_status sable_extract(sable_plan_t P) {
+  if (!P) return SABLE_ERR_INVALID;
+  if (P->sticky) return P->sticky;
+  if (P->extracted) return SABLE_ERR_ORDER;
+  try {
+    const Csr &C = P->canon;
+    const int64_t nnz = C.nnz();
+    std::vector<int32_t> region(nnz, -1);
+    std::vector<Segment> segs;   // acceptance order
+    std::vector<Block> blks;
+    for (auto &ex : P->extractors) {
+      const sable_extract_params &p = ex.second;
+      Csr R = residual(*P, false);
+      if (ex.first == SABLE_X_CSR) {
+        for (int64_t q = 0; q < R.nnz(); ++q) P->owner[R.id[q]] = OWN_CSR;
+      } else if (ex.first == SABLE_X_VDIA) {
+        for (const BandSeg &s : extract_bands(R, p)) {
+          const int32_t sid = (int32_t)segs.size();
+          segs.push_back({s.i0, s.i1 - s.i0, s.d - s.L, s.L + s.U + 1});
+          for (int64_t r = s.i0; r < s.i1; ++r)
+            for (int64_t q = R.rp[r]; q < R.rp[r + 1]; ++q) {
+              const int64_t o = (int64_t)R.ci[q] - r;
+              if (o >= s.d - s.L && o <= s.d + s.U) {
+                P->owner[R.id[q]] = OWN_VDIA;
+                region[R.id[q]] = sid;
+              }
+            }
+        }
+      } else {
+        Csr RT = residual(*P, true);
+        for (const BlockFound &b : partition_blocks(R, RT, p)) {
+          const int32_t bid = (int32_t)blks.size();
+          blks.push_back({b.r0, b.r1 - b.r0, b.c0, b.c1 - b.c0});
+          for (int64_t r = b.r0; r < b.r1; ++r)
+            for (int64_t q = R.rp[r]; q < R.rp[r + 1]; ++q)
+              if (R.ci[q] >= b.c0 && R.ci[q] < b.c1) {
+                P->owner[R.id[q]] = OWN_VBR;
+                region[R.id[q]] = bid;
+              }
+        }
+      }
+    }
+    for (int64_t k = 0; k < nnz; ++k)
+      if (P->owner[k] < 0) return fail(P, SABLE_ERR_INCOMPLETE);
+
+    Hybrid &H = P->hyb;
+    H.m = P->m;
+    H.n = P->n;
+    // order segments and blocks by first row; remember where each went
+    std::vector<int32_t> so(segs.size()), bo(blks.size());
+    std::iota(so.begin(), so.end(), 0);
+    std::iota(bo.begin(), bo.end(), 0);
+    std::stable_sort(so.begin(), so.end(), [&](int32_t a, int32_t b) {
+      return segs[a].row0 != segs[b].row0 ? segs[a].row0 < segs[b].row0 : segs[a].off_lo < segs[b].off_lo;
+    });
+    std::stable_sort(bo.begin(), bo.end(), [&](int32_t a, int32_t b) {
+      return blks[a].r0 != blks[b].r0 ? blks[a].r0 < blks[b].r0 : blks[a].c0 < blks[b].c0;
+    });
+    std::vector<int32_t> sidx(segs.size()), bidx(blks.size());
+    std::vector<int64_t> sptr(segs.size() + 1, 0), bptr(blks.size() + 1, 0);
+    H.segs.clear();
+    for (size_t t = 0; t < so.size(); ++t) {
+      sidx[so[t]] = (int32_t)t;
+      H.segs.push_back(segs[so[t]]);
+      sptr[t + 1] = sptr[t] + segs[so[t]].nrows * segs[so[t]].ndiag;
+    }
+    H.blks.clear();
+    for (size_t t = 0; t < bo.size(); ++t) {
+      bidx[bo[t]] = (int32_t)t;
+      H.blks.push_back(blks[bo[t]]);
+      bptr[t + 1] = bptr[t] + blks[bo[t]].nr * blks[bo[t]].nc;
+    }
+    H.vdia_canon.assign(sptr.back(), 0.0f);
+    H.vbr_canon.assign(bptr.back(), 0.0f);
+    H.crp.assign(P->m + 1, 0);
+    H.cci.clear();
+    H.ccv.clear();
+    int64_t nv = 0, nb = 0, nc = 0;
+    for (int64_t i = 0; i < C.m; ++i) {
+      for (int64_t k = C.rp[i]; k < C.rp[i + 1]; ++k) {
+        const int64_t j = C.ci[k];
+        if (P->owner[k] == OWN_VDIA) {
+          const int32_t s = sidx[region[k]];
+          const Segment &g = H.segs[s];
+          H.vdia_canon[sptr[s] + (j - i - g.off_lo) * g.nrows + (i - g.row0)] = P->cval[k];
+          ++nv;
+        } else if (P->owner[k] == OWN_VBR) {
+          const int32_t b = bidx[region[k]];
+          const Block &g = H.blks[b];
+          H.vbr_canon[bptr[b] + (j - g.c0) * g.nr + (i - g.r0)] = P->cval[k];
+          ++nb;
+        } else {
+          H.cci.push_back((int32_t)j);
+          H.ccv.push_back(P->cval[k]);
+          ++nc;
+        }
+      }
+      H.crp[i + 1] = (int64_t)H.cci.size();
+    }
+    if (nv + nb + nc != nnz) return fail(P, SABLE_ERR_INCOMPLETE);
+
+    sable_plan_stats &S = P->stats;
+    S = sable_plan_stats{};
+    S.m = P->m;
+    S.n = P->n;
+    S.nnz = nnz;
+    S.nnz_vdia = nv;
+    S.nnz_vbr = nb;
+    S.nnz_csr = nc;
+    S.n_segments = (int64_t)H.segs.size();
+    for (auto &g : H.segs) S.n_diagonals += g.ndiag;
+    S.vdia_cells = sptr.back();
+    S.n_blocks = (int64_t)H.blks.size();
+    S.vbr_cells = bptr.back();
+    S.csr_spmv_bytes = 8 * nnz + 4 * (P->m + 1) + 4 * P->n + 4 * P->m;
+    S.spmv_bytes = 4 * (S.vdia_cells + S.vbr_cells + nc) + 4 * nc + 4 * (P->m + 1) +
+                   32 * (S.n_segments + S.n_blocks) + 4 * P->n + 4 * P->m;
+  } catch (const std::bad_alloc &) {
+    return fail(P, SABLE_ERR_OOM);
+  }
+  P->extracted = true;
+  return SABLE_OK;
+}
+
+sable_status sable_plan_info(sable_plan_t P, sable_plan_stats *out) {
+  if (!P || !out) return SABLE_ERR_INVALID;
+  if (!P->extracted) return SABLE_ERR_ORDER;
+  *out = P->stats;
+  return SABLE_OK;
+}
+
+sable_status sable_plan_get_segments(sable_plan_t P, int64_t *out) {
+  if (!P || !out) return SABLE_ERR_INVALID;
+  if (!P->extracted) return SABLE_ERR_ORDER;
+  for (size_t s = 0; s < P->hyb.segs.size(); ++s) {
+    const Segment &g = P->hyb.segs[s];
+    out[4 * s] = g.row0;
+    out[4 * s + 1] = g.nrows;
+    out[4 * s + 2] = g.off_lo;
+    out[4 * s + 3] = g.ndiag;
+  }
+  return SABLE_OK;
+}
+
+sable_status sable_plan_get_blocks(sable_plan_t P, int64_t *out) {
+  if (!P || !out) return SABLE_ERR_INVALID;
+  if (!P->extracted) return SABLE_ERR_ORDER;
+  for (size_t b = 0; b < P->hyb.blks.size(); ++b) {
+    const Block &g = P->hyb.blks[b];
+    out[4 * b] = g.r0;
+    out[4 * b + 1] = g.nr;
+    out[4 * b + 2] = g.c0;
+    out[4 * b + 3] = g.nc;
+  }
+  return SABLE_OK;
+}
+
+sable_status sable_plan_get_vdia_values(sable_plan_t P, float *out) {
+  if (!P || (!out && !P->hyb.vdia_canon.empty())) return SABLE_ERR_INVALID;
+  if (!P->extracted) return SABLE_ERR_ORDER;
+  if (!P->hyb.vdia_canon.empty())
+    std::memcpy(out, P->hyb.vdia_canon.data(), P->hyb.vdia_canon.size() * sizeof(float));
+  return SABLE_OK;
+}
+
+sable_status sable_plan_get_vbr_values(sable_plan_t P, float *out) {
+  if (!P || (!out && !P->hyb.vbr_canon.empty())) return SABLE_ERR_INVALID;
+  if (!P->extracted) return SABLE_ERR_ORDER;
+  if (!P->hyb.vbr_canon.empty())
+    std::memcpy(out, P->hyb.vbr_canon.data(), P->hyb.vbr_canon.size() * sizeof(float));
+  return SABLE_OK;
+}
+
+sable_status sable_plan_get_csr(sable_plan_t P, int64_t *row_ptr, int32_t *col, float *val) {
+  if (!P || !row_ptr) return SABLE_ERR_INVALID;
+  if (!P->extracted) return SABLE_ERR_ORDER;
+  const Hybrid &H = P->hyb;
+  std::memcpy(row_ptr, H.crp.data(), H.crp.size() * sizeof(int64_t));
+  if (!H.cci.empty()) {
+    if (!col || !val) return SABLE_ERR_INVALID;
+    std::memcpy(col, H.cci.data(), H.cci.size() * sizeof(int32_t));
+    std::memcpy(val, H.ccv.data(), H.ccv.size() * sizeof(float));
+  }
+  return SABLE_OK;
+}
+
+sable_status sable_plan_set_tiling(sable_plan_t P, int32_t rows_per_item, int64_t item_bytes,
+                                   int32_t threads) {
+  if (!P) return SABLE_ERR_INVALID;
+  if (rows_per_item < 4 || rows_per_item > 1024 || rows_per_item % 4 || item_bytes < 64 ||
+      (threads != 128 && threads != 256 && threads != 512))
+    return SABLE_ERR_INVALID;
+  P->tiling.rows_per_item = rows_per_item;
+  P->tiling.item_bytes = item_bytes;
+  P->tiling.threads = threads;
+  return SABLE_OK;
+}
+
+sable_status sable_plan_status(sable_plan_t P) { return P ? P->sticky : SABLE_ERR_INVALID; }
+
+}  // extern "C"

@@ -1,0 +1,689 @@
+// Device side of libsable: table upload and the fused hybrid SpMV / SpMM
+// kernels (FP32).  One launch computes every format for a row tile ("item")
+// and writes each output row once, instead of the paper's sequence of
+// dispatches that each accumulate into a shared output (Section 3.4).
+//
+// Per item (rows [r0, r1)):
+//   A. VDIA: every segment touching the rows; a thread owns 4 consecutive
+//      rows and sweeps the segment's diagonals (Section 4.2.1 layout:
+//      diagonal-major, each run padded to 16-byte alignment), so value loads
+//      are float4 and x loads are consecutive across the warp.
+//   B. VBR: every block touching the rows; column-major blocks (Appendix B)
+//      give coalesced loads with lanes over rows and warps over columns.
+//   C. CSR remainder: the tile's entries form one contiguous range, streamed
+//      4 per thread with vector loads; a warp segmented scan merges partial
+//      row sums before they are added to the tile's row accumulators.
+//   The accumulators live in shared memory and are stored once per row.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "sable_internal.h"
+
+using namespace sable;
+
+namespace sable {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------ SpMV
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+spmv_hybrid_kernel(const DevHybrid A, const float *__restrict__ x, float *__restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int rows_max = A.spmv.rows_max;
+  float *ys = reinterpret_cast<float *>(smem_raw);
+  int *rps = reinterpret_cast<int *>(ys + rows_max);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = THREADS / 32;
+  const unsigned n = (unsigned)A.n;
+
+  for (int it = blockIdx.x; it < A.spmv.n; it += gridDim.x) {
+    const DevItem I = A.spmv.items[it];
+    const int r0 = I.r0, R = I.r1 - I.r0;
+    for (int i = tid; i <= R; i += THREADS) rps[i] = __ldg(A.rp + r0 + i);
+
+    // ---- A. VDIA: thread owns rows my .. my+3
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const int my = r0 + 4 * tid;
+    for (int q = I.seg_lo; q < I.seg_hi; ++q) {
+      const DevSeg s = A.segs[__ldg(A.spmv.iseg + q)];
+      const int ra = max(r0, s.row0), rb = min(I.r1, s.row0 + s.nrows);
+      if (my + 3 < ra || my >= rb) continue;
+      const bool g0 = my >= ra && my < rb, g1 = my + 1 >= ra && my + 1 < rb;
+      const bool g2 = my + 2 >= ra && my + 2 < rb, g3 = my + 3 >= ra && my + 3 < rb;
+      const float *vp = A.vdia + s.val_off + (my - s.base);
+      const int c0 = my + s.off_lo;
+#pragma unroll 4
+      for (int k = 0; k < s.ndiag; ++k) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(vp + (int64_t)k * s.ld));
+        const int c = c0 + k;
+        const float x0 = (g0 && (unsigned)c < n) ? __ldg(x + c) : 0.f;
+        const float x1 = (g1 && (unsigned)(c + 1) < n) ? __ldg(x + c + 1) : 0.f;
+        const float x2 = (g2 && (unsigned)(c + 2) < n) ? __ldg(x + c + 2) : 0.f;
+        const float x3 = (g3 && (unsigned)(c + 3) < n) ? __ldg(x + c + 3) : 0.f;
+        a0 = fmaf(v.x, x0, a0);
+        a1 = fmaf(v.y, x1, a1);
+        a2 = fmaf(v.z, x2, a2);
+        a3 = fmaf(v.w, x3, a3);
+      }
+    }
+    {
+      const int i = 4 * tid;
+      if (i < R) ys[i] = a0;
+      if (i + 1 < R) ys[i + 1] = a1;
+      if (i + 2 < R) ys[i + 2] = a2;
+      if (i + 3 < R) ys[i + 3] = a3;
+    }
+    __syncthreads();
+
+    // ---- B. VBR: lanes over rows, warps over columns
+    for (int q = I.blk_lo; q < I.blk_hi; ++q) {
+      const DevBlk b = A.blks[__ldg(A.spmv.iblk + q)];
+      const int ra = max(r0, b.r0), rb = min(I.r1, b.r0 + b.nr);
+      for (int rr = ra + lane; rr < rb; rr += 32) {
+        const float *bp = A.vbr + b.val_off + (rr - b.r0);
+        const float *xp = x + b.c0;
+        float acc = 0.f;
+        for (int c = warp; c < b.nc; c += NW) acc = fmaf(__ldg(bp + (int64_t)c * b.nr), __ldg(xp + c), acc);
+        atomicAdd(&ys[rr - r0], acc);
+      }
+    }
+
+    // ---- C. CSR remainder: 4 entries per thread, warp segmented scan
+    const int pb = rps[0], pe = rps[R];
+    for (int base = pb & ~3; base < pe; base += 4 * THREADS) {
+      const int p0 = base + 4 * tid;
+      int row = -1 - lane;
+      float run = 0.f;
+      if (p0 < pe && p0 + 4 > pb) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(A.cv + p0));
+        const int4 c = __ldg(reinterpret_cast<const int4 *>(A.ci + p0));
+        const int pf = max(p0, pb);
+        int lo = 0, hi = R;                 // rps[lo] <= pf < rps[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (rps[mid] <= pf) lo = mid;
+          else hi = mid;
+        }
+        int cur = lo, nxt = rps[lo + 1], cnt = 0;
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+        const int cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int pp = p0 + e;
+          if (pp >= pb && pp < pe) {
+            while (pp >= nxt) {
+              if (cnt) atomicAdd(&ys[cur], run);
+              run = 0.f;
+              cnt = 0;
+              ++cur;
+              nxt = rps[cur + 1];
+            }
+            run = fmaf(vv[e], __ldg(x + cc[e]), run);
+            ++cnt;
+          }
+        }
+        row = cur;
+      }
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const float s2 = __shfl_up_sync(kFull, run, d);
+        const int r2 = __shfl_up_sync(kFull, row, d);
+        if (lane >= d && r2 == row) run += s2;
+      }
+      const int rn = __shfl_down_sync(kFull, row, 1);
+      if (row >= 0 && (lane == 31 || rn != row)) atomicAdd(&ys[row], run);
+    }
+    __syncthreads();
+    for (int i = tid; i < R; i += THREADS) y[r0 + i] = ys[i];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ SpMM (FP32)
+template <int V> struct VecT;
+template <> struct VecT<4> {
+  using T = float4;
+  __device__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ static T load(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+  __device__ static void fma(T &a, float s, const T &b) {
+    a.x = fmaf(s, b.x, a.x); a.y = fmaf(s, b.y, a.y); a.z = fmaf(s, b.z, a.z); a.w = fmaf(s, b.w, a.w);
+  }
+  __device__ static void add_to(float *p, const T &a) {
+    p[0] += a.x; p[1] += a.y; p[2] += a.z; p[3] += a.w;
+  }
+  __device__ static void atomic_add_to(float *p, const T &a) {
+    atomicAdd(p, a.x); atomicAdd(p + 1, a.y); atomicAdd(p + 2, a.z); atomicAdd(p + 3, a.w);
+  }
+};
+template <> struct VecT<1> {
+  using T = float;
+  __device__ static T zero() { return 0.f; }
+  __device__ static T load(const float *p) { return __ldg(p); }
+  __device__ static void fma(T &a, float s, const T &b) { a = fmaf(s, b, a); }
+  __device__ static void add_to(float *p, const T &a) { p[0] += a; }
+  __device__ static void atomic_add_to(float *p, const T &a) { atomicAdd(p, a); }
+};
+
+// C[:, n0:n0+NT] for every item; V = 4 needs N, ldb, ldc multiples of 4 and
+// 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
+template <int THREADS, int V>
+__global__ void __launch_bounds__(THREADS)
+spmm_hybrid_kernel(const DevHybrid A, const float *__restrict__ B, int64_t ldb, float *__restrict__ C,
+                   int64_t ldc, int N) {
+  using Vt = VecT<V>;
+  using T = typename Vt::T;
+  constexpr int NT = 32 * V;
+  constexpr int NW = THREADS / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int rows_max = A.spmm.rows_max;
+  float *cs = reinterpret_cast<float *>(smem_raw);
+  int *rps = reinterpret_cast<int *>(cs + rows_max * NT);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n0 = blockIdx.y * NT;
+  const int lc = V * lane;                       // this lane's first column in the tile
+  const bool lane_ok = n0 + lc < N;
+  const unsigned n = (unsigned)A.n;
+
+  for (int it = blockIdx.x; it < A.spmm.n; it += gridDim.x) {
+    const DevItem I = A.spmm.items[it];
+    const int r0 = I.r0, R = I.r1 - I.r0;
+    for (int i = tid; i < R * NT; i += THREADS) cs[i] = 0.f;
+    for (int i = tid; i <= R; i += THREADS) rps[i] = __ldg(A.rp + r0 + i);
+    __syncthreads();
+
+    // ---- A. VDIA: item row i belongs to warp i % NW in phases A and B
+    for (int q = I.seg_lo; q < I.seg_hi; ++q) {
+      const DevSeg s = A.segs[__ldg(A.spmm.iseg + q)];
+      const int ia = max(r0, s.row0) - r0, ib = min(I.r1, s.row0 + s.nrows) - r0;
+      const int first = ia + ((warp - ia % NW) + NW) % NW;
+      for (int i = first; i < ib; i += NW) {
+        const int r = r0 + i;
+        T acc = Vt::zero();
+        const float *vp = A.vdia + s.val_off + (r - s.base);
+        for (int k = 0; k < s.ndiag; ++k) {
+          const int c = r + s.off_lo + k;
+          if ((unsigned)c >= n) continue;
+          const float v = __ldg(vp + (int64_t)k * s.ld);
+          if (lane_ok) Vt::fma(acc, v, Vt::load(B + (int64_t)c * ldb + n0 + lc));
+        }
+        if (lane_ok) Vt::add_to(cs + i * NT + lc, acc);
+      }
+    }
+    // ---- B. VBR (FP32 FMA)
+    for (int q = I.blk_lo; q < I.blk_hi; ++q) {
+      const DevBlk b = A.blks[__ldg(A.spmm.iblk + q)];
+      const int ia = max(r0, b.r0) - r0, ib = min(I.r1, b.r0 + b.nr) - r0;
+      const int first = ia + ((warp - ia % NW) + NW) % NW;
+      for (int i = first; i < ib; i += NW) {
+        const float *ap = A.vbr + b.val_off + (r0 + i - b.r0);
+        const float *bp = B + (int64_t)b.c0 * ldb + n0 + lc;
+        T acc = Vt::zero();
+        int c = 0;
+        for (; c + 4 <= b.nc; c += 4) {
+          const float w0 = __ldg(ap + (int64_t)c * b.nr), w1 = __ldg(ap + (int64_t)(c + 1) * b.nr);
+          const float w2 = __ldg(ap + (int64_t)(c + 2) * b.nr), w3 = __ldg(ap + (int64_t)(c + 3) * b.nr);
+          if (lane_ok) {
+            const T b0 = Vt::load(bp + (int64_t)c * ldb), b1 = Vt::load(bp + (int64_t)(c + 1) * ldb);
+            const T b2 = Vt::load(bp + (int64_t)(c + 2) * ldb), b3 = Vt::load(bp + (int64_t)(c + 3) * ldb);
+            Vt::fma(acc, w0, b0);
+            Vt::fma(acc, w1, b1);
+            Vt::fma(acc, w2, b2);
+            Vt::fma(acc, w3, b3);
+          }
+        }
+        for (; c < b.nc; ++c) {
+          const float w = __ldg(ap + (int64_t)c * b.nr);
+          if (lane_ok) Vt::fma(acc, w, Vt::load(bp + (int64_t)c * ldb));
+        }
+        if (lane_ok) Vt::add_to(cs + i * NT + lc, acc);
+      }
+    }
+    __syncthreads();
+
+    // ---- C. CSR remainder: the tile's entries split evenly over warps
+    const int pb = rps[0], pe = rps[R];
+    const int per = (pe - pb + NW - 1) / NW;
+    const int pa = pb + warp * per, pz = min(pe, pa + per);
+    if (pa < pz) {
+      int lo = 0, hi = R;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (rps[mid] <= pa) lo = mid;
+        else hi = mid;
+      }
+      int cur = lo, nxt = rps[lo + 1];
+      T acc = Vt::zero();
+      for (int base = pa; base < pz; base += 32) {
+        const int p = base + lane;
+        float v = 0.f;
+        int c = 0;
+        if (p < pz) {
+          v = __ldg(A.cv + p);
+          c = __ldg(A.ci + p);
+        }
+        const int cnt = min(32, pz - base);
+        for (int j = 0; j < cnt; j += 4) {
+          float vj[4];
+          int cj[4];
+          T bj[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            vj[u] = __shfl_sync(kFull, v, (j + u) & 31);
+            cj[u] = __shfl_sync(kFull, c, (j + u) & 31);
+            bj[u] = (lane_ok && j + u < cnt) ? Vt::load(B + (int64_t)cj[u] * ldb + n0 + lc) : Vt::zero();
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (j + u < cnt) {
+              const int pp = base + j + u;
+              if (pp >= nxt) {
+                if (lane_ok) Vt::atomic_add_to(cs + (cur)*NT + lc, acc);
+                acc = Vt::zero();
+                while (pp >= nxt) {
+                  ++cur;
+                  nxt = rps[cur + 1];
+                }
+              }
+              Vt::fma(acc, vj[u], bj[u]);
+            }
+          }
+        }
+      }
+      if (lane_ok) Vt::atomic_add_to(cs + cur * NT + lc, acc);
+    }
+    __syncthreads();
+    // ---- store the tile
+    if (lane_ok) {
+      for (int i = warp; i < R; i += NW) {
+        const float *src = cs + i * NT + lc;
+        float *dst = C + (int64_t)(r0 + i) * ldc + n0 + lc;
+        if (V == 4) {
+          *reinterpret_cast<float4 *>(dst) = *reinterpret_cast<const float4 *>(src);
+        } else {
+          dst[0] = src[0];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ host helpers
+struct HostItems {
+  std::vector<DevItem> items;
+  std::vector<int32_t> iseg, iblk;
+  int32_t rows_max = 0;
+};
+
+// Cut rows into tiles of at most rows_max rows (multiples of 4) whose summed
+// per-row cost stays near `target`; list the segments/blocks touching each.
+static HostItems build_items(int64_t m, const std::vector<Segment> &segs,
+                             const std::vector<Block> &blks, const std::vector<int64_t> &rp,
+                             int rows_max, int64_t target, bool spmm) {
+  std::vector<int64_t> vd(m + 1, 0), vb(m + 1, 0);
+  for (auto &s : segs) {
+    vd[s.row0] += s.ndiag;
+    vd[s.row0 + s.nrows] -= s.ndiag;
+  }
+  for (auto &b : blks) {
+    vb[b.r0] += b.nc;
+    vb[b.r0 + b.nr] -= b.nc;
+  }
+  for (int64_t i = 1; i <= m; ++i) {
+    vd[i] += vd[i - 1];
+    vb[i] += vb[i - 1];
+  }
+  auto cost = [&](int64_t i) -> int64_t {
+    const int64_t c = rp[i + 1] - rp[i];
+    return spmm ? 1 + vd[i] + vb[i] + c : 8 + 4 * vd[i] + 4 * vb[i] + 8 * c;
+  };
+  HostItems H;
+  size_t sp = 0, bp = 0;
+  std::vector<int32_t> as, ab;
+  int64_t r = 0;
+  while (r < m) {
+    const int64_t a = r;
+    int64_t acc = 0;
+    while (r < m && r - a < rows_max) {
+      const int64_t e = std::min<int64_t>(m, r + 4);
+      int64_t q = 0;
+      for (int64_t i = r; i < e; ++i) q += cost(i);
+      if (r > a && acc + q > target) break;
+      acc += q;
+      r = e;
+    }
+    const int64_t b = r;
+    DevItem it{};
+    it.r0 = (int32_t)a;
+    it.r1 = (int32_t)b;
+    while (sp < segs.size() && segs[sp].row0 < b) as.push_back((int32_t)sp++);
+    while (bp < blks.size() && blks[bp].r0 < b) ab.push_back((int32_t)bp++);
+    as.erase(std::remove_if(as.begin(), as.end(),
+                            [&](int32_t s) { return segs[s].row0 + segs[s].nrows <= a; }),
+             as.end());
+    ab.erase(std::remove_if(ab.begin(), ab.end(), [&](int32_t s) { return blks[s].r0 + blks[s].nr <= a; }),
+             ab.end());
+    it.seg_lo = (int32_t)H.iseg.size();
+    H.iseg.insert(H.iseg.end(), as.begin(), as.end());
+    it.seg_hi = (int32_t)H.iseg.size();
+    it.blk_lo = (int32_t)H.iblk.size();
+    H.iblk.insert(H.iblk.end(), ab.begin(), ab.end());
+    it.blk_hi = (int32_t)H.iblk.size();
+    H.items.push_back(it);
+    H.rows_max = std::max<int32_t>(H.rows_max, (int32_t)(b - a));
+  }
+  return H;
+}
+
+struct Piece {
+  size_t off;
+  const void *src;
+  size_t bytes;
+};
+
+struct Arena {
+  size_t off = 0;
+  std::vector<Piece> pieces;
+  size_t add(const void *src, size_t bytes) {
+    const size_t o = off;
+    off = (off + bytes + 255) & ~(size_t)255;
+    if (bytes) pieces.push_back({o, src, bytes});
+    return o;
+  }
+  size_t reserve(size_t bytes) { return add(nullptr, bytes); }
+};
+
+// Host staging kept alive by the plan until destroy (uploads are async).
+struct Staging {
+  std::vector<DevSeg> segs;
+  std::vector<float> vdia;
+  std::vector<DevBlk> blks;
+  std::vector<int32_t> rp, ci, prp, pci;
+  std::vector<float> cv, pcv;
+  HostItems it_v, it_m, pit_v, pit_m;
+};
+
+}  // namespace sable
+
+static sable_status cuda_fail(sable_plan_t P, cudaError_t e) {
+  (void)cudaGetLastError();
+  return fail(P, e == cudaErrorMemoryAllocation ? SABLE_ERR_OOM : SABLE_ERR_CUDA);
+}
+
+extern "C" {
+
+sable_status sable_plan_upload(sable_plan_t P, void *stream) {
+  if (!P) return SABLE_ERR_INVALID;
+  if (P->sticky) return P->sticky;
+  if (!P->extracted) return SABLE_ERR_ORDER;
+  if (P->tiling.rows_per_item > 4 * P->tiling.threads) return fail(P, SABLE_ERR_INVALID);
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(P, e);
+  if (P->dev_blob) {                       // re-upload (new tiling): release first
+    cudaFree(P->dev_blob);
+    P->dev_blob = nullptr;
+  }
+  Staging *S = nullptr;
+  try {
+    S = new Staging();
+    const Hybrid &H = P->hyb;
+    const Csr &Cn = P->canon;
+    // VDIA, padded runs
+    std::vector<int64_t> sptr(H.segs.size() + 1, 0);
+    for (size_t s = 0; s < H.segs.size(); ++s) sptr[s + 1] = sptr[s] + H.segs[s].nrows * H.segs[s].ndiag;
+    int64_t voff = 0;
+    for (size_t s = 0; s < H.segs.size(); ++s) {
+      const Segment &g = H.segs[s];
+      DevSeg d{};
+      d.row0 = (int32_t)g.row0;
+      d.nrows = (int32_t)g.nrows;
+      d.off_lo = (int32_t)g.off_lo;
+      d.ndiag = (int32_t)g.ndiag;
+      d.base = (int32_t)(g.row0 & ~(int64_t)3);
+      d.ld = (int32_t)(((g.row0 + g.nrows + 3) & ~(int64_t)3) - d.base);
+      d.val_off = voff;
+      S->segs.push_back(d);
+      voff += (int64_t)d.ld * d.ndiag;
+    }
+    S->vdia.assign(std::max<int64_t>(voff, 4), 0.0f);
+    for (size_t s = 0; s < H.segs.size(); ++s) {
+      const DevSeg &d = S->segs[s];
+      for (int64_t k = 0; k < d.ndiag; ++k)
+        for (int64_t r = 0; r < d.nrows; ++r)
+          S->vdia[d.val_off + k * d.ld + (d.row0 - d.base) + r] = H.vdia_canon[sptr[s] + k * d.nrows + r];
+    }
+    int64_t boff = 0;
+    for (const Block &b : H.blks) {
+      DevBlk d{};
+      d.r0 = (int32_t)b.r0;
+      d.nr = (int32_t)b.nr;
+      d.c0 = (int32_t)b.c0;
+      d.nc = (int32_t)b.nc;
+      d.val_off = boff;
+      d.bf_off = 0;
+      S->blks.push_back(d);
+      boff += b.nr * b.nc;
+    }
+    S->rp.assign(H.crp.begin(), H.crp.end());
+    S->ci.assign(H.cci.begin(), H.cci.end());
+    S->cv.assign(H.ccv.begin(), H.ccv.end());
+    S->ci.resize(S->ci.size() + 4, 0);
+    S->cv.resize(S->cv.size() + 4, 0.0f);
+    S->prp.assign(Cn.rp.begin(), Cn.rp.end());
+    S->pci.assign(Cn.ci.begin(), Cn.ci.end());
+    S->pcv.assign(P->cval.begin(), P->cval.end());
+    S->pci.resize(S->pci.size() + 4, 0);
+    S->pcv.resize(S->pcv.size() + 4, 0.0f);
+    const Tiling &T = P->tiling;
+    S->it_v = build_items(P->m, H.segs, H.blks, H.crp, T.rows_per_item, T.item_bytes, false);
+    S->it_m = build_items(P->m, H.segs, H.blks, H.crp, T.rows_per_item_mm, T.item_elems_mm, true);
+    const std::vector<Segment> no_s;
+    const std::vector<Block> no_b;
+    S->pit_v = build_items(P->m, no_s, no_b, Cn.rp, T.rows_per_item, T.item_bytes, false);
+    S->pit_m = build_items(P->m, no_s, no_b, Cn.rp, T.rows_per_item_mm, T.item_elems_mm, true);
+  } catch (const std::bad_alloc &) {
+    delete S;
+    return fail(P, SABLE_ERR_OOM);
+  }
+  Arena ar;
+  auto vec_bytes = [](const auto &v) { return v.size() * sizeof(v[0]); };
+  const size_t o_err = ar.reserve(256);
+  const size_t o_segs = ar.add(S->segs.data(), vec_bytes(S->segs));
+  const size_t o_vdia = ar.add(S->vdia.data(), vec_bytes(S->vdia));
+  const size_t o_blks = ar.add(S->blks.data(), vec_bytes(S->blks));
+  const size_t o_vbr = ar.add(P->hyb.vbr_canon.data(), vec_bytes(P->hyb.vbr_canon));
+  const size_t o_rp = ar.add(S->rp.data(), vec_bytes(S->rp));
+  const size_t o_ci = ar.add(S->ci.data(), vec_bytes(S->ci));
+  const size_t o_cv = ar.add(S->cv.data(), vec_bytes(S->cv));
+  const size_t o_prp = ar.add(S->prp.data(), vec_bytes(S->prp));
+  const size_t o_pci = ar.add(S->pci.data(), vec_bytes(S->pci));
+  const size_t o_pcv = ar.add(S->pcv.data(), vec_bytes(S->pcv));
+  size_t o_it[4][3];
+  HostItems *its[4] = {&S->it_v, &S->it_m, &S->pit_v, &S->pit_m};
+  for (int k = 0; k < 4; ++k) {
+    o_it[k][0] = ar.add(its[k]->items.data(), vec_bytes(its[k]->items));
+    o_it[k][1] = ar.add(its[k]->iseg.data(), vec_bytes(its[k]->iseg));
+    o_it[k][2] = ar.add(its[k]->iblk.data(), vec_bytes(its[k]->iblk));
+  }
+  char *blob = nullptr;
+  e = cudaMalloc(&blob, ar.off);
+  if (e != cudaSuccess) {
+    delete S;
+    return cuda_fail(P, e);
+  }
+  e = cudaMemsetAsync(blob, 0, 256, st);
+  for (const Piece &pc : ar.pieces)
+    if (e == cudaSuccess && pc.src) e = cudaMemcpyAsync(blob + pc.off, pc.src, pc.bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    delete S;
+    cudaFree(blob);
+    return cuda_fail(P, e);
+  }
+  auto items_of = [&](int k, const HostItems *h) {
+    DevItems d;
+    d.items = reinterpret_cast<const DevItem *>(blob + o_it[k][0]);
+    d.iseg = reinterpret_cast<const int32_t *>(blob + o_it[k][1]);
+    d.iblk = reinterpret_cast<const int32_t *>(blob + o_it[k][2]);
+    d.n = (int32_t)h->items.size();
+    d.rows_max = h->rows_max;
+    return d;
+  };
+  DevHybrid &D = P->dev;
+  D = DevHybrid{};
+  D.m = (int32_t)P->m;
+  D.n = (int32_t)P->n;
+  D.segs = reinterpret_cast<const DevSeg *>(blob + o_segs);
+  D.vdia = reinterpret_cast<const float *>(blob + o_vdia);
+  D.blks = reinterpret_cast<const DevBlk *>(blob + o_blks);
+  D.vbr = reinterpret_cast<const float *>(blob + o_vbr);
+  D.rp = reinterpret_cast<const int32_t *>(blob + o_rp);
+  D.ci = reinterpret_cast<const int32_t *>(blob + o_ci);
+  D.cv = reinterpret_cast<const float *>(blob + o_cv);
+  D.err = reinterpret_cast<int32_t *>(blob + o_err);
+  D.spmv = items_of(0, its[0]);
+  D.spmm = items_of(1, its[1]);
+  DevHybrid &Q = P->dev_plain;
+  Q = DevHybrid{};
+  Q.m = D.m;
+  Q.n = D.n;
+  Q.rp = reinterpret_cast<const int32_t *>(blob + o_prp);
+  Q.ci = reinterpret_cast<const int32_t *>(blob + o_pci);
+  Q.cv = reinterpret_cast<const float *>(blob + o_pcv);
+  Q.err = D.err;
+  Q.spmv = items_of(2, its[2]);
+  Q.spmm = items_of(3, its[3]);
+  P->stats.n_items = D.spmv.n;
+  delete S;
+  P->dev_blob = blob;
+  P->dev_bytes = ar.off;
+  P->device = dev;
+  cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  P->uploaded = true;
+  return SABLE_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ launches
+namespace {
+
+template <class K>
+int grid_for(K kernel, int threads, size_t smem, int items, int sm_count) {
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  (void)cudaGetLastError();
+  const int g = per_sm * std::max(sm_count, 1);
+  return std::max(1, std::min(items, g));
+}
+
+sable_status check_ready(sable_plan_t P) {
+  if (!P) return SABLE_ERR_INVALID;
+  if (P->sticky) return P->sticky;
+  if (!P->uploaded) return SABLE_ERR_ORDER;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cuda_fail(P, cudaErrorInvalidDevice);
+  if (dev != P->device) return SABLE_ERR_INVALID;
+  return SABLE_OK;
+}
+
+sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, const float *x, float *y, cudaStream_t st) {
+  if (D.m == 0) return SABLE_OK;
+  if (!y || (D.n > 0 && !x)) return SABLE_ERR_INVALID;
+  const int threads = P->tiling.threads;
+  const size_t smem = (size_t)D.spmv.rows_max * 4 + ((size_t)D.spmv.rows_max + 1) * 4;
+  if (threads == 128) {
+    auto k = spmv_hybrid_kernel<128>;
+    k<<<grid_for(k, 128, smem, D.spmv.n, P->sm_count), 128, smem, st>>>(D, x, y);
+  } else if (threads == 512) {
+    auto k = spmv_hybrid_kernel<512>;
+    k<<<grid_for(k, 512, smem, D.spmv.n, P->sm_count), 512, smem, st>>>(D, x, y);
+  } else {
+    auto k = spmv_hybrid_kernel<256>;
+    k<<<grid_for(k, 256, smem, D.spmv.n, P->sm_count), 256, smem, st>>>(D, x, y);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SABLE_OK : cuda_fail(P, e);
+}
+
+sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int64_t N, int64_t ldb,
+                         float *C, int64_t ldc, cudaStream_t st) {
+  if (N < 1 || ldb < N || ldc < N || N > (int64_t)65535 * 32) return SABLE_ERR_INVALID;
+  if (D.m == 0) return SABLE_OK;
+  if (!C || (D.n > 0 && !B)) return SABLE_ERR_INVALID;
+  const bool vec = N % 4 == 0 && ldb % 4 == 0 && ldc % 4 == 0 &&
+                   ((uintptr_t)B & 15) == 0 && ((uintptr_t)C & 15) == 0;
+  constexpr int TH = 256;
+  const int NT = vec ? 128 : 32;
+  const size_t smem = (size_t)D.spmm.rows_max * NT * 4 + ((size_t)D.spmm.rows_max + 1) * 4;
+  const int gy = (int)((N + NT - 1) / NT);
+  if (vec) {
+    auto k = spmm_hybrid_kernel<TH, 4>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
+    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
+  } else {
+    auto k = spmm_hybrid_kernel<TH, 1>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
+    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SABLE_OK : cuda_fail(P, e);
+}
+
+}  // namespace
+
+extern "C" {
+
+sable_status sable_spmv(sable_plan_t P, const float *x, float *y, void *stream) {
+  const sable_status s = check_ready(P);
+  if (s) return s;
+  return launch_spmv(P, P->dev, x, y, (cudaStream_t)stream);
+}
+
+sable_status sable_csr_spmv(sable_plan_t P, const float *x, float *y, void *stream) {
+  const sable_status s = check_ready(P);
+  if (s) return s;
+  return launch_spmv(P, P->dev_plain, x, y, (cudaStream_t)stream);
+}
+
+sable_status sable_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, float *C, int64_t ldc,
+                        sable_precision prec, void *stream) {
+  const sable_status s = check_ready(P);
+  if (s) return s;
+  if (prec == SABLE_BF16_BLOCKS) return SABLE_ERR_UNSUPPORTED;
+  if (prec != SABLE_FP32) return SABLE_ERR_INVALID;
+  return launch_spmm(P, P->dev, B, N, ldb, C, ldc, (cudaStream_t)stream);
+}
+
+sable_status sable_csr_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, float *C, int64_t ldc,
+                            void *stream) {
+  const sable_status s = check_ready(P);
+  if (s) return s;
+  return launch_spmm(P, P->dev_plain, B, N, ldb, C, ldc, (cudaStream_t)stream);
+}
+
+sable_status sable_plan_destroy(sable_plan_t P) {
+  if (!P) return SABLE_OK;
+  if (P->dev_blob) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != P->device) cudaSetDevice(P->device);
+    cudaFree(P->dev_blob);
+    if (cur >= 0 && cur != P->device) cudaSetDevice(cur);
+    (void)cudaGetLastError();
+  }
+  delete P;
+  return SABLE_OK;
+}
+
+}  // extern "C"

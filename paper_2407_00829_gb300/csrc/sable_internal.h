@@ -1,0 +1,143 @@
+// Internal declarations shared by the host C++ and CUDA translation units of
+// libsable.  Nothing here is part of the public ABI (include/sable.h).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/sable.h"
+
+namespace sable {
+
+// Owner tags of canonical entries.
+enum : int8_t { OWN_NONE = -1, OWN_VDIA = 0, OWN_VBR = 1, OWN_CSR = 2 };
+
+// Canonical matrix / residual in compressed-row form.  `id` maps each stored
+// entry back to its canonical index.
+struct Csr {
+  int64_t m = 0, n = 0;
+  std::vector<int64_t> rp;   // m + 1
+  std::vector<int32_t> ci;   // column (or row, for the transposed form)
+  std::vector<int64_t> id;   // canonical entry index
+  int64_t nnz() const { return rp.empty() ? 0 : rp.back(); }
+  // entries of line i with inner index in [lo, hi]
+  int64_t count(int64_t i, int64_t lo, int64_t hi) const;
+};
+
+// One VDIA segment: rows [row0, row0 + nrows), diagonals off_lo .. off_lo + ndiag - 1.
+struct Segment {
+  int64_t row0, nrows, off_lo, ndiag;
+};
+
+// One VBR block: rows [r0, r0 + nr), columns [c0, c0 + nc).
+struct Block {
+  int64_t r0, nr, c0, nc;
+};
+
+// ---- device-side tables (plain structs shared with the kernels) -------------
+struct DevSeg {          // 32 bytes
+  int32_t row0, nrows;   // segment rows
+  int32_t off_lo, ndiag; // consecutive offsets off_lo .. off_lo + ndiag - 1
+  int32_t base;          // row0 rounded down to a multiple of 4
+  int32_t ld;            // padded run length (multiple of 4)
+  int64_t val_off;       // start of the segment's runs in the value array (floats)
+};
+
+struct DevBlk {          // 32 bytes
+  int32_t r0, nr, c0, nc;
+  int64_t val_off;       // FP32 values, column-major, leading dimension nr
+  int64_t bf_off;        // BF16 tile-packed values (elements)
+};
+
+struct DevItem {         // 32 bytes: one row tile of a launch
+  int32_t r0, r1;        // rows [r0, r1), r0 a multiple of 4
+  int32_t seg_lo, seg_hi;// segments overlapping the rows
+  int32_t blk_lo, blk_hi;// blocks overlapping the rows
+  int32_t mat;           // matrix index (batched launches), 0 otherwise
+  int32_t pad;
+};
+
+// Row tiles of one launch: items, and per item the indices of the segments
+// (iseg[seg_lo, seg_hi)) and blocks (iblk[blk_lo, blk_hi)) touching its rows.
+struct DevItems {
+  const DevItem *items = nullptr;
+  const int32_t *iseg = nullptr;
+  const int32_t *iblk = nullptr;
+  int32_t n = 0;
+  int32_t rows_max = 0;          // largest r1 - r0
+};
+
+// Device copy of one hybrid matrix.
+struct DevHybrid {
+  int32_t m = 0, n = 0;
+  const DevSeg *segs = nullptr;
+  const float *vdia = nullptr;
+  const DevBlk *blks = nullptr;
+  const float *vbr = nullptr;
+  const uint16_t *vbr_bf16 = nullptr;
+  const float *vbr_scale = nullptr;  // per block power-of-two scale
+  const int32_t *rp = nullptr;   // CSR remainder row pointer (m + 1)
+  const int32_t *ci = nullptr;   // padded by 4 entries
+  const float *cv = nullptr;     // padded by 4 entries
+  DevItems spmv, spmm;
+  int32_t *err = nullptr;        // device error word (0 = ok)
+};
+
+// Host tiling knobs.
+struct Tiling {
+  int32_t rows_per_item = 512;   // SpMV row tile
+  int64_t item_bytes = 48 * 1024;
+  int32_t threads = 256;
+  int32_t rows_per_item_mm = 32; // SpMM row tile
+  int64_t item_elems_mm = 4096;  // stored cells + entries per SpMM tile
+};
+
+// Host-side extracted hybrid form and its device mirror.
+struct Hybrid {
+  int64_t m = 0, n = 0;
+  std::vector<Segment> segs;          // sorted by row0
+  std::vector<float> vdia_canon;      // Fig. 4 layout, no padding
+  std::vector<Block> blks;            // sorted by r0
+  std::vector<float> vbr_canon;       // column-major per block
+  std::vector<int64_t> crp;           // CSR remainder
+  std::vector<int32_t> cci;
+  std::vector<float> ccv;
+};
+
+}  // namespace sable
+
+// The opaque plan.
+struct sable_plan_s {
+  int64_t m = 0, n = 0;
+  sable::Csr canon;                    // canonical matrix (sorted, duplicates summed)
+  std::vector<float> cval;             // canonical values
+  std::vector<std::pair<sable_extractor, sable_extract_params>> extractors;
+  std::vector<int8_t> owner;           // per canonical entry
+  sable::Hybrid hyb;
+  sable::Tiling tiling;
+  bool extracted = false, uploaded = false;
+  sable_status sticky = SABLE_OK;
+  // device state (owned)
+  void *dev_blob = nullptr;            // one allocation holding every table
+  size_t dev_bytes = 0;
+  sable::DevHybrid dev;                // hybrid tables
+  sable::DevHybrid dev_plain;          // whole matrix as CSR (comparison kernel)
+  int32_t *dev_err = nullptr;
+  int device = -1;
+  int sm_count = 0;
+  sable_plan_stats stats{};
+};
+
+namespace sable {
+// host_plan.cpp
+sable_status fail(sable_plan_t p, sable_status s);
+// host_band.cpp: Algorithms 3 and 4; returns accepted segments (acceptance order)
+// as (row0, row_end, d, L, U).
+struct BandSeg { int64_t i0, i1, d, L, U, z; };
+std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p);
+// host_block.cpp: Algorithms 1 and 2; returns accepted blocks (acceptance order).
+struct BlockFound { int64_t r0, r1, c0, c1, nnz; };
+std::vector<BlockFound> partition_blocks(const Csr &R, const Csr &RT, const sable_extract_params &p);
+// threads used by the host extractors
+int host_threads();
+}  // namespace sable

@@ -1,0 +1,174 @@
+"""Host logic of the library (no GPU needed): the C ABI loads and exports every
+declared symbol, plan rules map to status codes, and the library's C++
+extractors produce exactly the oracle's segments, blocks, stored values and
+CSR remainder."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import extract as ox
+import paper_2407_00829_gb300 as sable
+import synth
+from conftest import ROOT, read_golden
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "sable.h")).read()
+    declared = set(re.findall(r"\b(sable_[a-z0-9_]+)\s*\(", hdr))
+    assert declared, "no declarations parsed"
+    L = sable.lib()
+    missing = [d for d in sorted(declared) if not hasattr(L, d)]
+    assert not missing, missing
+    assert set(sable.EXPORTED) <= declared
+
+
+def _to_ox_params(kind, kw):
+    p = ox.default_params(kind)
+    for k, v in (kw or {}).items():
+        setattr(p, k, v)
+    return p
+
+
+def _compare(A, extractors):
+    """Run the same plan through the library and the oracle; compare exactly."""
+    P = sable.plan_from(A, extractors, upload=False)
+    ex = ox.run_plan(A["m"], A["n"], A["row"], A["col"], A["val"],
+                     [(k, _to_ox_params(k, kw)) for k, kw in extractors])
+    segs = sorted(map(tuple, P.segments().tolist()))
+    blks = sorted(map(tuple, P.blocks().tolist()))
+    assert segs == sorted(ex.segments)
+    assert blks == sorted(ex.blocks)
+    info = P.info()
+    assert info["nnz"] == ex.rows.size
+    assert info["nnz_vdia"] == int(np.sum(ex.owner == ox.VDIA))
+    assert info["nnz_vbr"] == int(np.sum(ex.owner == ox.VBR))
+    assert info["nnz_csr"] == int(np.sum(ex.owner == ox.CSR))
+    # stored values, through the exact partition checker
+    vd, vb, cs = {}, {}, {}
+    vals = P.vdia_values()
+    k = 0
+    for (r0, nr, lo, nd) in P.segments().tolist():
+        for o in range(lo, lo + nd):
+            for r in range(r0, r0 + nr):
+                if 0 <= r + o < A["n"]:
+                    vd[(r, r + o)] = vals[k]
+                else:
+                    assert vals[k] == 0
+                k += 1
+    vals = P.vbr_values()
+    k = 0
+    for (r0, nr, c0, nc) in P.blocks().tolist():
+        for c in range(c0, c0 + nc):
+            for r in range(r0, r0 + nr):
+                vb[(r, c)] = vals[k]
+                k += 1
+    rp, ci, cv = P.csr()
+    for i in range(A["m"]):
+        for q in range(rp[i], rp[i + 1]):
+            assert (i, int(ci[q])) not in cs
+            cs[(i, int(ci[q]))] = cv[q]
+        assert list(ci[rp[i]:rp[i + 1]]) == sorted(ci[rp[i]:rp[i + 1]])
+    ox.check_partition(ex, vd, vb, cs)
+    P.close()
+    return ex
+
+
+def test_fig4_through_the_library():
+    g = read_golden("vdia_fig4.txt")
+    M = np.array(g["matrix"])
+    r, c = np.nonzero(M)
+    A = dict(m=10, n=10, row=r, col=c, val=M[r, c].astype(np.float32))
+    P = sable.plan_from(A, [(sable.VDIA, dict(delta=0.75, a_min=12, l_seg=3, count_min=3)),
+                            (sable.CSR, None)], upload=False)
+    assert P.segments().tolist() == [[1, 4, -1, 3], [6, 3, -6, 4]]
+    assert P.vdia_values().tolist() == g["val"]
+    assert P.info()["nnz_csr"] == 0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_three_formats_match_oracle(seed):
+    rng = np.random.default_rng(400 + seed)
+    m = 180
+    bands = [(o, int(rng.integers(0, 40)), int(rng.integers(80, 140))) for o in (-1, 0, 1, 2)]
+    bands.append((int(rng.integers(20, 60)), 0, 150))
+    blocks = [(120, 10, 30, 24, 0.85), (10, 130, 28, 30, 0.9), (60, 70, 20, 20, 0.7)]
+    A = synth.assemble(rng, m, m, bands=bands, blocks=blocks, n_scatter=500)
+    _compare(A, [(sable.VDIA, dict(delta=0.75, a_min=200, l_seg=16)),
+                 (sable.VBR, dict(delta=0.5, a_min=200, max_span=64, tile=8)),
+                 (sable.CSR, None)])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_block_partitioner_literal_whole_matrix(seed):
+    rng = np.random.default_rng(500 + seed)
+    A = synth.assemble(rng, 70, 64, blocks=[(5, 3, 18, 20, 0.9), (40, 30, 20, 25, 0.8)],
+                       n_scatter=150)
+    _compare(A, [(sable.VBR, dict(delta=0.5, a_min=150, max_span=70, tile=0)), (sable.CSR, None)])
+
+
+def test_vbr_before_vdia_order():
+    rng = np.random.default_rng(9)
+    A = synth.assemble(rng, 150, 150, bands=[(o, 0, 150) for o in (-1, 0, 1)],
+                       blocks=[(40, 40, 30, 30, 0.95)], n_scatter=200)
+    ex = _compare(A, [(sable.VBR, dict(a_min=300, max_span=64)),
+                      (sable.VDIA, dict(delta=0.75, a_min=100, l_seg=8)), (sable.CSR, None)])
+    assert ex.blocks and ex.segments
+
+
+def test_duplicates_and_explicit_zeros():
+    row = np.array([0, 0, 1, 1, 2, 2, 2], np.int32)
+    col = np.array([1, 1, 0, 2, 2, 2, 0], np.int32)
+    val = np.array([0.5, 0.25, 0.0, 1.0, 1e8, 1.0, -3.0], np.float32)
+    A = dict(m=3, n=3, row=row, col=col, val=val)
+    P = sable.plan_from(A, [(sable.CSR, None)], upload=False)
+    rp, ci, cv = P.csr()
+    assert rp.tolist() == [0, 1, 3, 5]
+    assert ci.tolist() == [1, 0, 2, 0, 2]
+    assert cv.tolist() == [0.75, 0.0, 1.0, -3.0, np.float32(1e8 + 1.0)]
+    rows, cols, vals = ox.canonicalize(3, 3, row, col, val)
+    assert vals.tolist() == cv[np.lexsort((ci, np.repeat(np.arange(3), np.diff(rp))))].tolist()
+
+
+def test_status_codes():
+    L = sable.lib()
+    with pytest.raises(sable.SableError) as e:
+        sable.Plan(3, 3, [0, 5], [0, 0], [1.0, 2.0])           # row out of range
+    assert e.value.status == 1
+    with pytest.raises(sable.SableError) as e:
+        sable.Plan(-1, 3, [], [], [])
+    assert e.value.status == 1
+    P = sable.Plan(4, 4, [0, 1], [0, 3], [1.0, 2.0])
+    with pytest.raises(sable.SableError) as e:
+        P.info()                                                # before extract
+    assert e.value.status == 5
+    P.add_extractor(sable.VDIA)
+    with pytest.raises(sable.SableError) as e:
+        P.extract()                                             # no catch-all extractor
+    assert e.value.status == 4
+    assert P.status() == 4                                      # sticky
+    P.close()
+    P = sable.Plan(4, 4, [0], [0], [1.0])
+    with pytest.raises(sable.SableError) as e:
+        P.add_extractor(sable.VBR, delta=0.0)
+    assert e.value.status == 1
+    P.add_extractor(sable.CSR).extract()
+    with pytest.raises(sable.SableError) as e:
+        P.add_extractor(sable.CSR)                              # after extract
+    assert e.value.status == 5
+    with pytest.raises(sable.SableError) as e:
+        P.extract()
+    assert e.value.status == 5
+    P.close()
+    assert L.sable_status_string(4) == b"incomplete plan: entries left unclaimed"
+
+
+def test_empty_matrix_plans():
+    for m, n in [(0, 0), (5, 0), (0, 7), (6, 6)]:
+        P = sable.plan_from(dict(m=m, n=n, row=np.zeros(0), col=np.zeros(0), val=np.zeros(0)),
+                            [(sable.VDIA, None), (sable.VBR, None), (sable.CSR, None)], upload=False)
+        info = P.info()
+        assert info["nnz"] == 0 and info["n_segments"] == 0 and info["n_blocks"] == 0
+        P.close()

@@ -254,9 +254,7 @@ def main():
     # cuSPARSE CSR (library) on the same matrix, same rotation
     cus_ms = None
     try:
-        rp, ci, cv = [], [], []
         cs = []
-        rows, cols, vals = None, None, None
         order = np.lexsort((A["col"], A["row"]))
         rows, cols, vals = A["row"][order], A["col"][order], A["val"][order]
         crow = np.zeros(A["m"] + 1, dtype=np.int64)
@@ -269,8 +267,16 @@ def main():
             torch.mv(cs[i % reps], xs[i % reps])
         cus_ms = timed(lambda i: torch.mv(cs[i], xs[i]), min(args.steps, 500))
         del cs
-    except Exception as e:  # library comparison point only
-        cus_err = repr(e)
+    except Exception:  # library comparison point only; reported as null
+        cus_ms = None
+
+    # gather ceiling of this device: random 4-byte reads of an x of the same size
+    gcount = max(info["nnz_csr"], 1 << 20)
+    gout = torch.zeros(1, device=dev)
+    for _ in range(3):
+        sable.probe_gather(xs[0], gcount, gout, stream)
+    g_ms = timed(lambda i: sable.probe_gather(xs[i], gcount, gout, stream), 50)
+    gather_peak = gcount / (g_ms * 1e-3) / 1e9
 
     # end to end: pinned host x -> device, SpMV through the public API, y -> pinned host
     xh = torch.from_numpy(x_np).pin_memory()
@@ -330,6 +336,12 @@ def main():
                          "traffic": traffic, "kernel": "spmv_hybrid_kernel<256>",
                          "achieved_def": "spmv_bytes per launch / mean launch time over the timed region"},
             "pct_hbm_peak": 100.0 * gbs / peak,
+            "gather_roofline": {
+                "what": "random 4-byte gathers of x by the CSR remainder, one 32-byte L2 sector each; "
+                        "ceiling measured live with sable_probe_gather (hash indices, same n)",
+                "csr_gathers_per_step": info["nnz_csr"], "peak_gathers_per_s": gather_peak * 1e9,
+                "time_at_peak_us": info["nnz_csr"] / (gather_peak * 1e9) * 1e6,
+                "frac_of_step": (info["nnz_csr"] / (gather_peak * 1e9)) / (ms * 1e-3)},
             "plain_csr": {"kernel": "library CSR kernel, whole matrix", "ms_per_step": ms_plain,
                           "GB/s_hybrid_bytes": nbytes / (ms_plain * 1e-3) / 1e9,
                           "GB/s_own_bytes": info["csr_spmv_bytes"] / (ms_plain * 1e-3) / 1e9},

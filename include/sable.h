@@ -61,7 +61,7 @@ typedef enum { SABLE_FP32 = 0, SABLE_BF16_BLOCKS = 1 } sable_precision;
  *                0.75 for bands)
  *   a_min        minimum area of a block / of a band candidate (2500)
  *   l_seg        minimum rows of a VDIA segment (Algorithm 4)
- *   w_max        largest ribbon half-width FitRibbon may reach
+ *   w_max        largest ribbon half-width FitRibbon may reach (<= 512)
  *   d_max        largest |diagonal offset| considered (0 = all)
  *   count_min    entries a diagonal needs to be a candidate (0 = ceil(delta*l_seg))
  *   coverage_min share of entries blocks must cover, else none are kept (0.08)
@@ -163,12 +163,20 @@ sable_status sable_plan_get_vdia_values(sable_plan_t plan, float *out);
 sable_status sable_plan_get_vbr_values(sable_plan_t plan, float *out);
 sable_status sable_plan_get_csr(sable_plan_t plan, int64_t *row_ptr, int32_t *col, float *val);
 
-/* Tuning of the row tiles ("items") one launch works on.  rows_per_item is a
- * multiple of 4 in [4, 1024]; item_bytes is the target algorithmic bytes per
- * tile; threads is 128, 256 or 512.  Takes effect at the next upload.
- * Errors: SABLE_ERR_INVALID. */
-sable_status sable_plan_set_tiling(sable_plan_t plan, int32_t rows_per_item, int64_t item_bytes,
-                                   int32_t threads);
+/* Tuning of the row tiles one launch works on; takes effect at the next
+ * upload.  spmv_rows: rows of an SpMV tile, a multiple of 4 in [4, 1024];
+ * spmv_bytes: target algorithmic bytes per SpMV tile; spmm_rows: rows of an
+ * SpMM tile, a multiple of 4 in [4, 256]; spmm_elems: target stored cells +
+ * entries per SpMM tile.  Errors: SABLE_ERR_INVALID. */
+sable_status sable_plan_set_tiling(sable_plan_t plan, int32_t spmv_rows, int64_t spmv_bytes,
+                                   int32_t spmm_rows, int64_t spmm_elems);
+
+/* Calibration: `count` random 4-byte reads of x[0..n) (device), indices from a
+ * fixed hash reduced modulo n, one kernel launch on `stream`; `out` (device,
+ * one float) may be written.  Timing it gives the device's rate of random
+ * single-word gathers, the ceiling of the CSR part of SpMV on matrices with
+ * scattered entries.  No counterpart in the paper.  Errors: SABLE_ERR_INVALID. */
+sable_status sable_probe_gather(const float *x, int64_t n, int64_t count, float *out, void *stream);
 
 /* First error recorded on the plan (SABLE_OK if none). */
 sable_status sable_plan_status(sable_plan_t plan);

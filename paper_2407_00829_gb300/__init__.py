@@ -29,6 +29,7 @@ EXPORTED = [
     "sable_plan_info", "sable_plan_get_segments", "sable_plan_get_blocks",
     "sable_plan_get_vdia_values", "sable_plan_get_vbr_values", "sable_plan_get_csr",
     "sable_plan_set_tiling", "sable_plan_status", "sable_plan_destroy", "sable_status_string",
+    "sable_probe_gather",
 ]
 
 
@@ -79,10 +80,11 @@ def lib():
             "sable_plan_get_vdia_values": ([p, p], i32),
             "sable_plan_get_vbr_values": ([p, p], i32),
             "sable_plan_get_csr": ([p, p, p, p], i32),
-            "sable_plan_set_tiling": ([p, i32, i64, i32], i32),
+            "sable_plan_set_tiling": ([p, i32, i64, i32, i64], i32),
             "sable_plan_status": ([p], i32),
             "sable_plan_destroy": ([p], i32),
             "sable_status_string": ([i32], ctypes.c_char_p),
+            "sable_probe_gather": ([p, i64, i64, p, p], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -166,8 +168,9 @@ class Plan:
         _check(lib().sable_extract(self._h), "sable_extract")
         return self
 
-    def set_tiling(self, rows_per_item=512, item_bytes=48 * 1024, threads=256):
-        _check(lib().sable_plan_set_tiling(self._h, rows_per_item, item_bytes, threads), "set_tiling")
+    def set_tiling(self, spmv_rows=512, spmv_bytes=48 * 1024, spmm_rows=32, spmm_elems=4096):
+        _check(lib().sable_plan_set_tiling(self._h, spmv_rows, spmv_bytes, spmm_rows, spmm_elems),
+               "set_tiling")
         return self
 
     def upload(self, stream=None):
@@ -233,6 +236,12 @@ class Plan:
 
     def status(self) -> int:
         return lib().sable_plan_status(self._h)
+
+
+def probe_gather(x, count: int, out, stream=None):
+    """Launch the random-gather calibration kernel (see include/sable.h)."""
+    _check(lib().sable_probe_gather(_dptr(x), x.numel(), int(count), _dptr(out), _stream_handle(stream)),
+           "sable_probe_gather")
 
 
 def plan_from(A: dict, extractors, tiling: Optional[dict] = None, upload: bool = True, stream=None) -> Plan:

@@ -136,7 +136,7 @@ sable_status sable_plan_add_extractor(sable_plan_t P, sable_extractor kind,
   sable_extract_params p;
   sable_default_params(kind, &p);
   if (params) p = *params;
-  if (!(p.delta > 0.0 && p.delta <= 1.0) || p.a_min < 1 || p.l_seg < 1 || p.w_max < 0 ||
+  if (!(p.delta > 0.0 && p.delta <= 1.0) || p.a_min < 1 || p.l_seg < 1 || p.w_max < 0 || p.w_max > 512 ||
       p.d_max < 0 || p.count_min < 0 || !(p.coverage_min >= 0.0) || p.max_span < 1 ||
       p.tile < 0)
     return SABLE_ERR_INVALID;
@@ -330,15 +330,16 @@ sable_status sable_plan_get_csr(sable_plan_t P, int64_t *row_ptr, int32_t *col, 
   return SABLE_OK;
 }
 
-sable_status sable_plan_set_tiling(sable_plan_t P, int32_t rows_per_item, int64_t item_bytes,
-                                   int32_t threads) {
+sable_status sable_plan_set_tiling(sable_plan_t P, int32_t spmv_rows, int64_t spmv_bytes,
+                                   int32_t spmm_rows, int64_t spmm_elems) {
   if (!P) return SABLE_ERR_INVALID;
-  if (rows_per_item < 4 || rows_per_item > 1024 || rows_per_item % 4 || item_bytes < 64 ||
-      (threads != 128 && threads != 256 && threads != 512))
+  if (spmv_rows < 4 || spmv_rows > kRangeRows || spmv_rows % 4 || spmv_bytes < 64 || spmm_rows < 4 ||
+      spmm_rows > 256 || spmm_rows % 4 || spmm_elems < 1)
     return SABLE_ERR_INVALID;
-  P->tiling.rows_per_item = rows_per_item;
-  P->tiling.item_bytes = item_bytes;
-  P->tiling.threads = threads;
+  P->tiling.rows_per_item = spmv_rows;
+  P->tiling.item_bytes = spmv_bytes;
+  P->tiling.rows_per_item_mm = spmm_rows;
+  P->tiling.item_elems_mm = spmm_elems;
   return SABLE_OK;
 }
 

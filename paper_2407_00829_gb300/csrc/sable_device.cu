@@ -1,18 +1,16 @@
-// Device side of libsable: table upload and the fused hybrid SpMV / SpMM
-// kernels (FP32).  One launch computes every format for a row tile ("item")
-// and writes each output row once, instead of the paper's sequence of
-// dispatches that each accumulate into a shared output (Section 3.4).
+// Device side of libsable: table upload, the fused hybrid SpMM kernel (FP32)
+// and the C-ABI compute entry points.  (The SpMV kernel is in sable_spmv.cu.)
+// One launch computes every format for a row tile ("item") and writes each
+// output row once, instead of the paper's sequence of dispatches that each
+// accumulate into a shared output (Section 3.4).
 //
-// Per item (rows [r0, r1)):
-//   A. VDIA: every segment touching the rows; a thread owns 4 consecutive
-//      rows and sweeps the segment's diagonals (Section 4.2.1 layout:
-//      diagonal-major, each run padded to 16-byte alignment), so value loads
-//      are float4 and x loads are consecutive across the warp.
-//   B. VBR: every block touching the rows; column-major blocks (Appendix B)
-//      give coalesced loads with lanes over rows and warps over columns.
-//   C. CSR remainder: the tile's entries form one contiguous range, streamed
-//      4 per thread with vector loads; a warp segmented scan merges partial
-//      row sums before they are added to the tile's row accumulators.
+// SpMM, per item (rows [r0, r1)) and column tile of B/C:
+//   A. VDIA: every segment touching the rows (Section 4.2.1 layout); a warp
+//      owns a row, lanes own columns, each band value is reused over the
+//      tile's columns.
+//   B. VBR: every block touching the rows; column-major blocks (Appendix B).
+//   C. CSR remainder: the tile's entries split evenly over warps; lanes own
+//      columns; partial rows are merged with shared atomics.
 //   The accumulators live in shared memory and are stored once per row.
 #include <cuda_runtime.h>
 
@@ -27,121 +25,6 @@ using namespace sable;
 namespace sable {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-// ------------------------------------------------------------------ SpMV
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
-spmv_hybrid_kernel(const DevHybrid A, const float *__restrict__ x, float *__restrict__ y) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int rows_max = A.spmv.rows_max;
-  float *ys = reinterpret_cast<float *>(smem_raw);
-  int *rps = reinterpret_cast<int *>(ys + rows_max);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = THREADS / 32;
-  const unsigned n = (unsigned)A.n;
-
-  for (int it = blockIdx.x; it < A.spmv.n; it += gridDim.x) {
-    const DevItem I = A.spmv.items[it];
-    const int r0 = I.r0, R = I.r1 - I.r0;
-    for (int i = tid; i <= R; i += THREADS) rps[i] = __ldg(A.rp + r0 + i);
-
-    // ---- A. VDIA: thread owns rows my .. my+3
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    const int my = r0 + 4 * tid;
-    for (int q = I.seg_lo; q < I.seg_hi; ++q) {
-      const DevSeg s = A.segs[__ldg(A.spmv.iseg + q)];
-      const int ra = max(r0, s.row0), rb = min(I.r1, s.row0 + s.nrows);
-      if (my + 3 < ra || my >= rb) continue;
-      const bool g0 = my >= ra && my < rb, g1 = my + 1 >= ra && my + 1 < rb;
-      const bool g2 = my + 2 >= ra && my + 2 < rb, g3 = my + 3 >= ra && my + 3 < rb;
-      const float *vp = A.vdia + s.val_off + (my - s.base);
-      const int c0 = my + s.off_lo;
-#pragma unroll 4
-      for (int k = 0; k < s.ndiag; ++k) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(vp + (int64_t)k * s.ld));
-        const int c = c0 + k;
-        const float x0 = (g0 && (unsigned)c < n) ? __ldg(x + c) : 0.f;
-        const float x1 = (g1 && (unsigned)(c + 1) < n) ? __ldg(x + c + 1) : 0.f;
-        const float x2 = (g2 && (unsigned)(c + 2) < n) ? __ldg(x + c + 2) : 0.f;
-        const float x3 = (g3 && (unsigned)(c + 3) < n) ? __ldg(x + c + 3) : 0.f;
-        a0 = fmaf(v.x, x0, a0);
-        a1 = fmaf(v.y, x1, a1);
-        a2 = fmaf(v.z, x2, a2);
-        a3 = fmaf(v.w, x3, a3);
-      }
-    }
-    {
-      const int i = 4 * tid;
-      if (i < R) ys[i] = a0;
-      if (i + 1 < R) ys[i + 1] = a1;
-      if (i + 2 < R) ys[i + 2] = a2;
-      if (i + 3 < R) ys[i + 3] = a3;
-    }
-    __syncthreads();
-
-    // ---- B. VBR: lanes over rows, warps over columns
-    for (int q = I.blk_lo; q < I.blk_hi; ++q) {
-      const DevBlk b = A.blks[__ldg(A.spmv.iblk + q)];
-      const int ra = max(r0, b.r0), rb = min(I.r1, b.r0 + b.nr);
-      for (int rr = ra + lane; rr < rb; rr += 32) {
-        const float *bp = A.vbr + b.val_off + (rr - b.r0);
-        const float *xp = x + b.c0;
-        float acc = 0.f;
-        for (int c = warp; c < b.nc; c += NW) acc = fmaf(__ldg(bp + (int64_t)c * b.nr), __ldg(xp + c), acc);
-        atomicAdd(&ys[rr - r0], acc);
-      }
-    }
-
-    // ---- C. CSR remainder: 4 entries per thread, warp segmented scan
-    const int pb = rps[0], pe = rps[R];
-    for (int base = pb & ~3; base < pe; base += 4 * THREADS) {
-      const int p0 = base + 4 * tid;
-      int row = -1 - lane;
-      float run = 0.f;
-      if (p0 < pe && p0 + 4 > pb) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(A.cv + p0));
-        const int4 c = __ldg(reinterpret_cast<const int4 *>(A.ci + p0));
-        const int pf = max(p0, pb);
-        int lo = 0, hi = R;                 // rps[lo] <= pf < rps[hi]
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (rps[mid] <= pf) lo = mid;
-          else hi = mid;
-        }
-        int cur = lo, nxt = rps[lo + 1], cnt = 0;
-        const float vv[4] = {v.x, v.y, v.z, v.w};
-        const int cc[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int pp = p0 + e;
-          if (pp >= pb && pp < pe) {
-            while (pp >= nxt) {
-              if (cnt) atomicAdd(&ys[cur], run);
-              run = 0.f;
-              cnt = 0;
-              ++cur;
-              nxt = rps[cur + 1];
-            }
-            run = fmaf(vv[e], __ldg(x + cc[e]), run);
-            ++cnt;
-          }
-        }
-        row = cur;
-      }
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const float s2 = __shfl_up_sync(kFull, run, d);
-        const int r2 = __shfl_up_sync(kFull, row, d);
-        if (lane >= d && r2 == row) run += s2;
-      }
-      const int rn = __shfl_down_sync(kFull, row, 1);
-      if (row >= 0 && (lane == 31 || rn != row)) atomicAdd(&ys[row], run);
-    }
-    __syncthreads();
-    for (int i = tid; i < R; i += THREADS) y[r0 + i] = ys[i];
-    __syncthreads();
-  }
-}
 
 // ------------------------------------------------------------------ SpMM (FP32)
 template <int V> struct VecT;
@@ -316,6 +199,8 @@ spmm_hybrid_kernel(const DevHybrid A, const float *__restrict__ B, int64_t ldb, 
 struct HostItems {
   std::vector<DevItem> items;
   std::vector<int32_t> iseg, iblk;
+  std::vector<DevSeg> pseg;
+  std::vector<DevBlk> pblk;
   int32_t rows_max = 0;
 };
 
@@ -373,6 +258,12 @@ static HostItems build_items(int64_t m, const std::vector<Segment> &segs,
     it.blk_lo = (int32_t)H.iblk.size();
     H.iblk.insert(H.iblk.end(), ab.begin(), ab.end());
     it.blk_hi = (int32_t)H.iblk.size();
+    it.pb = (int32_t)rp[a];
+    it.pe = (int32_t)rp[b];
+    int64_t vc = 0;
+    for (int32_t q : as) vc += (std::min(b, segs[q].row0 + segs[q].nrows) - std::max(a, segs[q].row0)) * segs[q].ndiag;
+    for (int32_t q : ab) vc += (std::min(b, blks[q].r0 + blks[q].nr) - std::max(a, blks[q].r0)) * blks[q].nc;
+    it.vcells = (int32_t)std::min<int64_t>(vc, INT32_MAX);
     H.items.push_back(it);
     H.rows_max = std::max<int32_t>(H.rows_max, (int32_t)(b - a));
   }
@@ -420,7 +311,6 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   if (!P) return SABLE_ERR_INVALID;
   if (P->sticky) return P->sticky;
   if (!P->extracted) return SABLE_ERR_ORDER;
-  if (P->tiling.rows_per_item > 4 * P->tiling.threads) return fail(P, SABLE_ERR_INVALID);
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -473,13 +363,13 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
     S->rp.assign(H.crp.begin(), H.crp.end());
     S->ci.assign(H.cci.begin(), H.cci.end());
     S->cv.assign(H.ccv.begin(), H.ccv.end());
-    S->ci.resize(S->ci.size() + 4, 0);
-    S->cv.resize(S->cv.size() + 4, 0.0f);
+    S->ci.resize(S->ci.size() + kCsrPad, 0);
+    S->cv.resize(S->cv.size() + kCsrPad, 0.0f);
     S->prp.assign(Cn.rp.begin(), Cn.rp.end());
     S->pci.assign(Cn.ci.begin(), Cn.ci.end());
     S->pcv.assign(P->cval.begin(), P->cval.end());
-    S->pci.resize(S->pci.size() + 4, 0);
-    S->pcv.resize(S->pcv.size() + 4, 0.0f);
+    S->pci.resize(S->pci.size() + kCsrPad, 0);
+    S->pcv.resize(S->pcv.size() + kCsrPad, 0.0f);
     const Tiling &T = P->tiling;
     S->it_v = build_items(P->m, H.segs, H.blks, H.crp, T.rows_per_item, T.item_bytes, false);
     S->it_m = build_items(P->m, H.segs, H.blks, H.crp, T.rows_per_item_mm, T.item_elems_mm, true);
@@ -504,9 +394,13 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   const size_t o_prp = ar.add(S->prp.data(), vec_bytes(S->prp));
   const size_t o_pci = ar.add(S->pci.data(), vec_bytes(S->pci));
   const size_t o_pcv = ar.add(S->pcv.data(), vec_bytes(S->pcv));
-  size_t o_it[4][3];
+  size_t o_it[4][6];
   HostItems *its[4] = {&S->it_v, &S->it_m, &S->pit_v, &S->pit_m};
   for (int k = 0; k < 4; ++k) {
+    for (int32_t q : its[k]->iseg) its[k]->pseg.push_back(S->segs[q]);
+    for (int32_t q : its[k]->iblk) its[k]->pblk.push_back(S->blks[q]);
+    o_it[k][4] = ar.add(its[k]->pseg.data(), vec_bytes(its[k]->pseg));
+    o_it[k][5] = ar.add(its[k]->pblk.data(), vec_bytes(its[k]->pblk));
     o_it[k][0] = ar.add(its[k]->items.data(), vec_bytes(its[k]->items));
     o_it[k][1] = ar.add(its[k]->iseg.data(), vec_bytes(its[k]->iseg));
     o_it[k][2] = ar.add(its[k]->iblk.data(), vec_bytes(its[k]->iblk));
@@ -531,6 +425,8 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
     d.items = reinterpret_cast<const DevItem *>(blob + o_it[k][0]);
     d.iseg = reinterpret_cast<const int32_t *>(blob + o_it[k][1]);
     d.iblk = reinterpret_cast<const int32_t *>(blob + o_it[k][2]);
+    d.pseg = reinterpret_cast<const DevSeg *>(blob + o_it[k][4]);
+    d.pblk = reinterpret_cast<const DevBlk *>(blob + o_it[k][5]);
     d.n = (int32_t)h->items.size();
     d.rows_max = h->rows_max;
     return d;
@@ -595,25 +491,6 @@ sable_status check_ready(sable_plan_t P) {
   return SABLE_OK;
 }
 
-sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, const float *x, float *y, cudaStream_t st) {
-  if (D.m == 0) return SABLE_OK;
-  if (!y || (D.n > 0 && !x)) return SABLE_ERR_INVALID;
-  const int threads = P->tiling.threads;
-  const size_t smem = (size_t)D.spmv.rows_max * 4 + ((size_t)D.spmv.rows_max + 1) * 4;
-  if (threads == 128) {
-    auto k = spmv_hybrid_kernel<128>;
-    k<<<grid_for(k, 128, smem, D.spmv.n, P->sm_count), 128, smem, st>>>(D, x, y);
-  } else if (threads == 512) {
-    auto k = spmv_hybrid_kernel<512>;
-    k<<<grid_for(k, 512, smem, D.spmv.n, P->sm_count), 512, smem, st>>>(D, x, y);
-  } else {
-    auto k = spmv_hybrid_kernel<256>;
-    k<<<grid_for(k, 256, smem, D.spmv.n, P->sm_count), 256, smem, st>>>(D, x, y);
-  }
-  const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? SABLE_OK : cuda_fail(P, e);
-}
-
 sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int64_t N, int64_t ldb,
                          float *C, int64_t ldc, cudaStream_t st) {
   if (N < 1 || ldb < N || ldc < N || N > (int64_t)65535 * 32) return SABLE_ERR_INVALID;
@@ -647,13 +524,13 @@ extern "C" {
 sable_status sable_spmv(sable_plan_t P, const float *x, float *y, void *stream) {
   const sable_status s = check_ready(P);
   if (s) return s;
-  return launch_spmv(P, P->dev, x, y, (cudaStream_t)stream);
+  return launch_spmv(P, P->dev, false, x, y, (cudaStream_t)stream);
 }
 
 sable_status sable_csr_spmv(sable_plan_t P, const float *x, float *y, void *stream) {
   const sable_status s = check_ready(P);
   if (s) return s;
-  return launch_spmv(P, P->dev_plain, x, y, (cudaStream_t)stream);
+  return launch_spmv(P, P->dev_plain, true, x, y, (cudaStream_t)stream);
 }
 
 sable_status sable_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, float *C, int64_t ldc,

@@ -7,6 +7,9 @@
 
 #include "../../include/sable.h"
 
+struct CUstream_st;
+typedef CUstream_st *cudaStream_t_;   // cudaStream_t without including the runtime header
+
 namespace sable {
 
 // Owner tags of canonical entries.
@@ -49,12 +52,14 @@ struct DevBlk {          // 32 bytes
   int64_t bf_off;        // BF16 tile-packed values (elements)
 };
 
-struct DevItem {         // 32 bytes: one row tile of a launch
+struct DevItem {         // 48 bytes: one row tile of a launch
   int32_t r0, r1;        // rows [r0, r1), r0 a multiple of 4
   int32_t seg_lo, seg_hi;// segments overlapping the rows
   int32_t blk_lo, blk_hi;// blocks overlapping the rows
   int32_t mat;           // matrix index (batched launches), 0 otherwise
-  int32_t pad;
+  int32_t pb, pe;        // CSR remainder entries of the rows: [pb, pe)
+  int32_t vcells;        // VDIA + VBR cells of the tile's rows
+  int32_t pad[2];
 };
 
 // Row tiles of one launch: items, and per item the indices of the segments
@@ -63,6 +68,8 @@ struct DevItems {
   const DevItem *items = nullptr;
   const int32_t *iseg = nullptr;
   const int32_t *iblk = nullptr;
+  const DevSeg *pseg = nullptr;    // copies of segs[iseg[k]] (one load per piece)
+  const DevBlk *pblk = nullptr;    // copies of blks[iblk[k]]
   int32_t n = 0;
   int32_t rows_max = 0;          // largest r1 - r0
 };
@@ -77,18 +84,23 @@ struct DevHybrid {
   const uint16_t *vbr_bf16 = nullptr;
   const float *vbr_scale = nullptr;  // per block power-of-two scale
   const int32_t *rp = nullptr;   // CSR remainder row pointer (m + 1)
-  const int32_t *ci = nullptr;   // padded by 4 entries
-  const float *cv = nullptr;     // padded by 4 entries
+  const int32_t *ci = nullptr;   // padded by kCsrPad entries
+  const float *cv = nullptr;     // padded by kCsrPad entries
   DevItems spmv, spmm;
   int32_t *err = nullptr;        // device error word (0 = ok)
 };
 
+// Largest SpMV row tile (one CTA of 256 threads, 4 rows per thread) and the
+// zero padding after the CSR arrays that lets vector reads run past the last
+// entry.
+constexpr int kRangeRows = 1024;
+constexpr int kCsrPad = 8;
+
 // Host tiling knobs.
 struct Tiling {
-  int32_t rows_per_item = 512;   // SpMV row tile
+  int32_t rows_per_item = 512;   // SpMV row tile (<= kRangeRows, multiple of 4)
   int64_t item_bytes = 48 * 1024;
-  int32_t threads = 256;
-  int32_t rows_per_item_mm = 32; // SpMM row tile
+  int32_t rows_per_item_mm = 32; // SpMM row tile (<= 256, multiple of 4)
   int64_t item_elems_mm = 4096;  // stored cells + entries per SpMM tile
 };
 
@@ -140,4 +152,7 @@ struct BlockFound { int64_t r0, r1, c0, c1, nnz; };
 std::vector<BlockFound> partition_blocks(const Csr &R, const Csr &RT, const sable_extract_params &p);
 // threads used by the host extractors
 int host_threads();
+// sable_spmv.cu
+sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const float *x, float *y,
+                         cudaStream_t_ st);
 }  // namespace sable

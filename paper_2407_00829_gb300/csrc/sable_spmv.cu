@@ -1,0 +1,170 @@
+// Hybrid VDIA+VBR+CSR SpMV: one launch over a table of row tiles.
+//
+// A CTA owns a row tile [r0, r1) (at most 4 x kThreads rows) and writes each
+// of its rows of y exactly once (row ownership; the paper instead accumulates
+// every dispatch into a shared output, Section 3.4).  Per tile:
+//   A. VDIA: every segment piece touching the rows (Section 4.2.1 layout:
+//      diagonal-major runs, padded to 16-byte alignment); a thread owns 4
+//      consecutive rows, so each diagonal's values arrive as one float4 and x
+//      is read as 4 consecutive words.  Sums stay in registers, then seed the
+//      tile's row accumulators in shared memory.
+//   B. VBR: every block touching the rows (column-major, Appendix B); lanes
+//      own rows, warps split the columns, partial sums go in with shared
+//      atomics.
+//   C. CSR remainder: the tile's entries are one contiguous range, streamed
+//      4 per thread with vector loads; a thread finds the row of its first
+//      entry by binary search in the tile's row pointers (shared memory),
+//      sums runs of equal rows, and a warp segmented scan merges partial sums
+//      across lanes before the shared atomics.
+// Eight CTAs per SM work on different tiles, so one tile's VDIA phase
+// overlaps other tiles' gathers.  On GB300 the CSR gathers of x (random 4-byte
+// reads, one 32-byte L2 sector each) and the streamed arrays share the
+// L2-to-SM sector bandwidth, which bounds this kernel (see the bench report).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "sable_internal.h"
+
+namespace sable {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kThreads = 256;
+
+template <bool PLAIN>
+__global__ void __launch_bounds__(kThreads, 8)
+spmv_hybrid_kernel(const DevHybrid A, const float *__restrict__ x, float *__restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const DevItems &T = A.spmv;
+  const int rows_max = T.rows_max;
+  float *ys = reinterpret_cast<float *>(smem_raw);
+  int *rps = reinterpret_cast<int *>(ys + rows_max);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kThreads / 32;
+  const unsigned n = (unsigned)A.n;
+
+  for (int it = blockIdx.x; it < T.n; it += gridDim.x) {
+    const DevItem I = T.items[it];
+    const int r0 = I.r0, R = I.r1 - I.r0;
+    for (int i = tid; i <= R; i += kThreads) rps[i] = __ldg(A.rp + r0 + i);
+
+    // ---- A. VDIA: thread owns rows my .. my+3
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const int my = r0 + 4 * tid;
+    if (!PLAIN)
+      for (int q = I.seg_lo; q < I.seg_hi; ++q) {
+        const DevSeg s = T.pseg[q];
+        const int ra = max(r0, s.row0), rb = min(I.r1, s.row0 + s.nrows);
+        if (my + 3 < ra || my >= rb) continue;
+        const bool g0 = my >= ra && my < rb, g1 = my + 1 >= ra && my + 1 < rb;
+        const bool g2 = my + 2 >= ra && my + 2 < rb, g3 = my + 3 >= ra && my + 3 < rb;
+        const float *vp = A.vdia + s.val_off + (my - s.base);
+        const int c0 = my + s.off_lo;
+#pragma unroll 4
+        for (int k = 0; k < s.ndiag; ++k) {
+          const float4 v = __ldg(reinterpret_cast<const float4 *>(vp + (size_t)k * s.ld));
+          const int c = c0 + k;
+          const float x0 = (g0 && (unsigned)c < n) ? __ldg(x + c) : 0.f;
+          const float x1 = (g1 && (unsigned)(c + 1) < n) ? __ldg(x + c + 1) : 0.f;
+          const float x2 = (g2 && (unsigned)(c + 2) < n) ? __ldg(x + c + 2) : 0.f;
+          const float x3 = (g3 && (unsigned)(c + 3) < n) ? __ldg(x + c + 3) : 0.f;
+          a0 = fmaf(v.x, x0, a0);
+          a1 = fmaf(v.y, x1, a1);
+          a2 = fmaf(v.z, x2, a2);
+          a3 = fmaf(v.w, x3, a3);
+        }
+      }
+    {
+      const int i = 4 * tid;
+      if (i < R) ys[i] = a0;
+      if (i + 1 < R) ys[i + 1] = a1;
+      if (i + 2 < R) ys[i + 2] = a2;
+      if (i + 3 < R) ys[i + 3] = a3;
+    }
+    __syncthreads();
+
+    // ---- B. VBR: lanes over rows, warps over columns
+    if (!PLAIN)
+      for (int q = I.blk_lo; q < I.blk_hi; ++q) {
+        const DevBlk b = T.pblk[q];
+        const int ra = max(r0, b.r0), rb = min(I.r1, b.r0 + b.nr);
+        for (int rr = ra + lane; rr < rb; rr += 32) {
+          const float *bp = A.vbr + b.val_off + (rr - b.r0);
+          const float *xp = x + b.c0;
+          float acc = 0.f;
+          for (int c = warp; c < b.nc; c += NW) acc = fmaf(__ldg(bp + (size_t)c * b.nr), __ldg(xp + c), acc);
+          atomicAdd(&ys[rr - r0], acc);
+        }
+      }
+
+    // ---- C. CSR remainder: 4 entries per thread, warp segmented scan
+    const int pb = rps[0], pe = rps[R];
+    for (int base = pb & ~3; base < pe; base += 4 * kThreads) {
+      const int p0 = base + 4 * tid;
+      int row = -1 - lane;
+      float run = 0.f;
+      if (p0 < pe && p0 + 4 > pb) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(A.cv + p0));
+        const int4 c = __ldg(reinterpret_cast<const int4 *>(A.ci + p0));
+        const int pf = max(p0, pb);
+        int lo = 0, hi = R;                 // rps[lo] <= pf < rps[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (rps[mid] <= pf) lo = mid;
+          else hi = mid;
+        }
+        int cur = lo, nxt = rps[lo + 1], cnt = 0;
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+        const int cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int pp = p0 + e;
+          if (pp >= pb && pp < pe) {
+            while (pp >= nxt) {
+              if (cnt) atomicAdd(&ys[cur], run);
+              run = 0.f;
+              cnt = 0;
+              ++cur;
+              nxt = rps[cur + 1];
+            }
+            run = fmaf(vv[e], __ldg(x + cc[e]), run);
+            ++cnt;
+          }
+        }
+        row = cur;
+      }
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const float s2 = __shfl_up_sync(kFull, run, d);
+        const int r2 = __shfl_up_sync(kFull, row, d);
+        if (lane >= d && r2 == row) run += s2;
+      }
+      const int rn = __shfl_down_sync(kFull, row, 1);
+      if (row >= 0 && (lane == 31 || rn != row)) atomicAdd(&ys[row], run);
+    }
+    __syncthreads();
+    for (int i = tid; i < R; i += kThreads) y[r0 + i] = ys[i];
+    __syncthreads();
+  }
+}
+
+sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const float *x, float *y,
+                         cudaStream_t_ st) {
+  if (D.m == 0) return SABLE_OK;
+  if (!y || (D.n > 0 && !x)) return SABLE_ERR_INVALID;
+  if (D.spmv.rows_max > 4 * kThreads) return fail(P, SABLE_ERR_INVALID);
+  const size_t smem = (size_t)D.spmv.rows_max * 4 + ((size_t)D.spmv.rows_max + 1) * 4;
+  auto k = plain ? spmv_hybrid_kernel<true> : spmv_hybrid_kernel<false>;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int grid = std::max(1, std::min(D.spmv.n, per_sm * std::max(P->sm_count, 1)));
+  k<<<grid, kThreads, smem, st>>>(D, x, y);
+  if (cudaGetLastError() != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(P, SABLE_ERR_CUDA);
+  }
+  return SABLE_OK;
+}
+
+}  // namespace sable

@@ -114,14 +114,15 @@ def assemble(rng, m, n, bands=(), blocks=(), n_scatter=0, row_lengths=None, valu
 
 # ---------------------------------------------------------------- the five workloads
 def blocks_bands_scatter_4096(seed=1001, values="uniform"):
-    """4096 x 4096: eight dense 64 x 64 blocks at 64-aligned positions on distinct
-    block rows and block columns, bands at offsets 0 and +-17 each over a random
-    contiguous 30-90 % of the rows, and 0.1 % uniformly scattered entries.
-    Values U[-1, 1]."""
+    """4096 x 4096: eight dense 64 x 64 blocks at 64-aligned positions on distinct,
+    pairwise non-adjacent block rows and block columns (so that the block
+    partitioner's disjointness rules can recover each of them), bands at
+    offsets 0 and +-17 each over a random contiguous 30-90 % of the rows, and
+    0.1 % uniformly scattered entries.  Values U[-1, 1]."""
     rng = np.random.default_rng(seed)
     n = 4096
-    br = rng.choice(n // 64, 8, replace=False)
-    bc = rng.choice(n // 64, 8, replace=False)
+    br = 2 * rng.choice(n // 128, 8, replace=False)
+    bc = 2 * rng.choice(n // 128, 8, replace=False)
     blocks = [(int(a) * 64, int(b) * 64, 64, 64, 1.0) for a, b in zip(br, bc)]
     bands = []
     for off in (0, 17, -17):

@@ -84,9 +84,9 @@ def test_spmv_small(case, plan):
     P.close()
 
 
-@pytest.mark.parametrize("tiling", [dict(rows_per_item=4, item_bytes=64, threads=128),
-                                    dict(rows_per_item=1024, item_bytes=1 << 20, threads=256),
-                                    dict(rows_per_item=36, item_bytes=300, threads=512)])
+@pytest.mark.parametrize("tiling", [dict(spmv_rows=4, spmv_bytes=64, spmm_rows=4, spmm_elems=1),
+                                    dict(spmv_rows=1024, spmv_bytes=1 << 22, spmm_rows=256, spmm_elems=1 << 20),
+                                    dict(spmv_rows=36, spmv_bytes=300, spmm_rows=12, spmm_elems=100)])
 def test_spmv_integer_exact_any_tiling(tiling):
     rng = np.random.default_rng(42)
     m, n = 1501, 1203

@@ -53,7 +53,7 @@ template <> struct VecT<1> {
 
 // C[:, n0:n0+NT] for every item; V = 4 needs N, ldb, ldc multiples of 4 and
 // 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
-template <int THREADS, int V>
+template <int THREADS, int V, bool VBRC>
 __global__ void __launch_bounds__(THREADS)
 spmm_hybrid_kernel(const DevHybrid A, const float *__restrict__ B, int64_t ldb, float *__restrict__ C,
                    int64_t ldc, int N) {
@@ -96,7 +96,16 @@ spmm_hybrid_kernel(const DevHybrid A, const float *__restrict__ B, int64_t ldb, 
         if (lane_ok) Vt::add_to(cs + i * NT + lc, acc);
       }
     }
-    // ---- B. VBR (FP32 FMA)
+    // ---- B. VBR: already multiplied on the tensor cores into C (VBRC), or FP32 FMA
+    if (VBRC) {
+      for (int q = I.blk_lo; q < I.blk_hi; ++q) {
+        const DevBlk b = A.spmm.pblk[q];
+        const int ia = max(r0, b.r0) - r0, ib = min(I.r1, b.r0 + b.nr) - r0;
+        const int first = ia + ((warp - ia % NW) + NW) % NW;
+        for (int i = first; i < ib; i += NW)
+          if (lane_ok) Vt::add_to(cs + i * NT + lc, Vt::load(C + (int64_t)(r0 + i) * ldc + n0 + lc));
+      }
+    } else
     for (int q = I.blk_lo; q < I.blk_hi; ++q) {
       const DevBlk b = A.blks[__ldg(A.spmm.iblk + q)];
       const int ia = max(r0, b.r0) - r0, ib = min(I.r1, b.r0 + b.nr) - r0;
@@ -293,7 +302,9 @@ struct Staging {
   std::vector<DevSeg> segs;
   std::vector<float> vdia;
   std::vector<DevBlk> blks;
-  std::vector<int32_t> rp, ci, prp, pci;
+  std::vector<int32_t> rp, ci, prp, pci, tc_pairs;
+  std::vector<uint16_t> vbr_bf16;
+  std::vector<float> vbr_scale;
   std::vector<float> cv, pcv;
   HostItems it_v, it_m, pit_v, pit_m;
 };
@@ -360,6 +371,12 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
       S->blks.push_back(d);
       boff += b.nr * b.nc;
     }
+    {
+      std::vector<int64_t> offs;
+      pack_vbr_bf16(H.blks, H.vbr_canon, S->vbr_bf16, S->vbr_scale, offs);
+      for (size_t b = 0; b < S->blks.size(); ++b) S->blks[b].bf_off = offs[b];
+      vbr_tc_pairs(H.blks, S->tc_pairs);
+    }
     S->rp.assign(H.crp.begin(), H.crp.end());
     S->ci.assign(H.cci.begin(), H.cci.end());
     S->cv.assign(H.ccv.begin(), H.ccv.end());
@@ -388,6 +405,9 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   const size_t o_vdia = ar.add(S->vdia.data(), vec_bytes(S->vdia));
   const size_t o_blks = ar.add(S->blks.data(), vec_bytes(S->blks));
   const size_t o_vbr = ar.add(P->hyb.vbr_canon.data(), vec_bytes(P->hyb.vbr_canon));
+  const size_t o_bf16 = ar.add(S->vbr_bf16.data(), vec_bytes(S->vbr_bf16));
+  const size_t o_scale = ar.add(S->vbr_scale.data(), vec_bytes(S->vbr_scale));
+  const size_t o_pairs = ar.add(S->tc_pairs.data(), vec_bytes(S->tc_pairs));
   const size_t o_rp = ar.add(S->rp.data(), vec_bytes(S->rp));
   const size_t o_ci = ar.add(S->ci.data(), vec_bytes(S->ci));
   const size_t o_cv = ar.add(S->cv.data(), vec_bytes(S->cv));
@@ -439,6 +459,10 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   D.vdia = reinterpret_cast<const float *>(blob + o_vdia);
   D.blks = reinterpret_cast<const DevBlk *>(blob + o_blks);
   D.vbr = reinterpret_cast<const float *>(blob + o_vbr);
+  D.vbr_bf16 = reinterpret_cast<const uint16_t *>(blob + o_bf16);
+  D.vbr_scale = reinterpret_cast<const float *>(blob + o_scale);
+  D.tc_pairs = reinterpret_cast<const int32_t *>(blob + o_pairs);
+  D.n_tc_pairs = (int32_t)(S->tc_pairs.size() / 2);
   D.rp = reinterpret_cast<const int32_t *>(blob + o_rp);
   D.ci = reinterpret_cast<const int32_t *>(blob + o_ci);
   D.cv = reinterpret_cast<const float *>(blob + o_cv);
@@ -492,7 +516,7 @@ sable_status check_ready(sable_plan_t P) {
 }
 
 sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int64_t N, int64_t ldb,
-                         float *C, int64_t ldc, cudaStream_t st) {
+                         float *C, int64_t ldc, bool vbrc, cudaStream_t st) {
   if (N < 1 || ldb < N || ldc < N || N > (int64_t)65535 * 32) return SABLE_ERR_INVALID;
   if (D.m == 0) return SABLE_OK;
   if (!C || (D.n > 0 && !B)) return SABLE_ERR_INVALID;
@@ -502,13 +526,23 @@ sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int
   const int NT = vec ? 128 : 32;
   const size_t smem = (size_t)D.spmm.rows_max * NT * 4 + ((size_t)D.spmm.rows_max + 1) * 4;
   const int gy = (int)((N + NT - 1) / NT);
-  if (vec) {
-    auto k = spmm_hybrid_kernel<TH, 4>;
+  if (vec && vbrc) {
+    auto k = spmm_hybrid_kernel<TH, 4, true>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
+    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
+  } else if (vbrc) {
+    auto k = spmm_hybrid_kernel<TH, 1, true>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
+    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
+  } else if (vec) {
+    auto k = spmm_hybrid_kernel<TH, 4, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
     k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
   } else {
-    auto k = spmm_hybrid_kernel<TH, 1>;
+    auto k = spmm_hybrid_kernel<TH, 1, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
     k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
@@ -537,16 +571,21 @@ sable_status sable_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, 
                         sable_precision prec, void *stream) {
   const sable_status s = check_ready(P);
   if (s) return s;
-  if (prec == SABLE_BF16_BLOCKS) return SABLE_ERR_UNSUPPORTED;
-  if (prec != SABLE_FP32) return SABLE_ERR_INVALID;
-  return launch_spmm(P, P->dev, B, N, ldb, C, ldc, (cudaStream_t)stream);
+  if (prec != SABLE_FP32 && prec != SABLE_BF16_BLOCKS) return SABLE_ERR_INVALID;
+  const bool bf16 = prec == SABLE_BF16_BLOCKS && P->dev.n_tc_pairs > 0;
+  if (bf16) {
+    if (N < 1 || ldb < N || ldc < N || !B || !C) return SABLE_ERR_INVALID;
+    const sable_status s2 = launch_vbr_tc(P, P->dev, B, ldb, C, ldc, (int)N, (cudaStream_t)stream);
+    if (s2) return s2;
+  }
+  return launch_spmm(P, P->dev, B, N, ldb, C, ldc, bf16, (cudaStream_t)stream);
 }
 
 sable_status sable_csr_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, float *C, int64_t ldc,
                             void *stream) {
   const sable_status s = check_ready(P);
   if (s) return s;
-  return launch_spmm(P, P->dev_plain, B, N, ldb, C, ldc, (cudaStream_t)stream);
+  return launch_spmm(P, P->dev_plain, B, N, ldb, C, ldc, false, (cudaStream_t)stream);
 }
 
 sable_status sable_plan_destroy(sable_plan_t P) {

@@ -83,6 +83,8 @@ struct DevHybrid {
   const float *vbr = nullptr;
   const uint16_t *vbr_bf16 = nullptr;
   const float *vbr_scale = nullptr;  // per block power-of-two scale
+  const int32_t *tc_pairs = nullptr; // (block, 128-row tile) pairs for the tensor-core path
+  int32_t n_tc_pairs = 0;
   const int32_t *rp = nullptr;   // CSR remainder row pointer (m + 1)
   const int32_t *ci = nullptr;   // padded by kCsrPad entries
   const float *cv = nullptr;     // padded by kCsrPad entries
@@ -152,6 +154,12 @@ struct BlockFound { int64_t r0, r1, c0, c1, nnz; };
 std::vector<BlockFound> partition_blocks(const Csr &R, const Csr &RT, const sable_extract_params &p);
 // threads used by the host extractors
 int host_threads();
+// sable_tc.cu: BF16 VBR blocks on the tensor cores
+void pack_vbr_bf16(const std::vector<Block> &blks, const std::vector<float> &canon,
+                   std::vector<uint16_t> &packed, std::vector<float> &scales, std::vector<int64_t> &offs);
+void vbr_tc_pairs(const std::vector<Block> &blks, std::vector<int32_t> &pairs);
+sable_status launch_vbr_tc(sable_plan_t P, const DevHybrid &D, const float *B, int64_t ldb, float *C, int64_t ldc,
+                           int N, cudaStream_t_ st);
 // sable_spmv.cu
 sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const float *x, float *y,
                          cudaStream_t_ st);

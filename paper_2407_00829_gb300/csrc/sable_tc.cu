@@ -1,0 +1,317 @@
+// VBR blocks of SpMM on the 5th-generation tensor cores (tcgen05), BF16
+// operands with FP32 accumulation in tensor memory (TMEM).
+//
+// Each VBR block (Appendix B) is a dense nr x nc matrix; its SpMM part is the
+// dense product C[r0:r0+nr, :] = Blk * B[c0:c0+nc, :].  Blocks are stored at
+// upload as bf16(a / s_b), rounded to nearest even, with the per-block
+// power-of-two scale s_b = 2^ceil(log2 max|a|), cut into tiles of 128 rows x
+// 64 columns laid out exactly as the tensor core reads shared memory (the
+// canonical K-major layout without swizzle: 8 x 8 "core matrices" of 128
+// contiguous bytes, adjacent along K 128 bytes apart, adjacent along M 1024
+// bytes apart).
+//
+// One CTA (4 warps) computes one job = (block, 128-row tile, 128-column tile
+// of B/C).  Per 64-wide K step: a TMA bulk copy brings the A tile (16 KB),
+// the 128 threads convert the matching 64 x 128 slice of B from FP32 to BF16
+// (round to nearest even) into the same layout (B as an N x K K-major
+// operand), and one thread issues four tcgen05.mma (M=128, N=128, K=16) into
+// a 128-column FP32 accumulator in TMEM; tcgen05.commit signals an mbarrier
+// when they finish.  The epilogue reads the accumulator with tcgen05.ld
+// (warp w owns TMEM lanes / rows 32w..32w+31), multiplies by s_b and writes
+// the block's rows of C.  Every wait is bounded; on time-out the kernel
+// records SABLE_ERR_TIMEOUT, skips the rest of its job, frees its TMEM and
+// returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "sable_internal.h"
+
+namespace sable {
+
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTileM = 128, kTileN = 128, kTileK = 64;
+constexpr int kTileBytes = kTileM * kTileK * 2;        // 16 KB, A and B tiles alike
+constexpr unsigned kTmemCols = 128;
+constexpr long long kTcWait = 4000000000LL;            // ~2 s
+
+struct TcShared {
+  alignas(1024) unsigned char a[kTileBytes];
+  alignas(1024) unsigned char b[kTileBytes];
+  uint64_t bar_a;     // A tile landed
+  uint64_t bar_mma;   // MMAs of the K step finished
+  uint32_t tmem_base;
+  int dead;
+};
+
+__device__ __forceinline__ unsigned su32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool bar_try(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, unsigned parity) {
+  if (bar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!bar_try(bar, parity))
+    if (clock64() - t0 > kTcWait) return false;
+  return true;
+}
+
+// Shared-memory matrix descriptor: canonical K-major layout, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(const void *p, unsigned lbo, unsigned sbo) {
+  const uint64_t addr = su32(p);
+  return ((addr & 0x3FFFFull) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: D = FP32, A = B = BF16, both K-major, M = N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+vbr_tc_kernel(const DevHybrid A, int n_jobs, int ntn, const float *__restrict__ B, int64_t ldb,
+              float *__restrict__ C, int64_t ldc, int N) {
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  // align the working area to 1024 bytes
+  TcShared &S = *reinterpret_cast<TcShared *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.bar_a)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.bar_mma)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    S.dead = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem_base;
+  unsigned ph_a = 0, ph_m = 0;
+
+  for (int job = blockIdx.x; job < n_jobs; job += gridDim.x) {
+    const int pair = job / ntn, n0 = (job - pair * ntn) * kTileN;
+    const int bi = A.tc_pairs[2 * pair], t = A.tc_pairs[2 * pair + 1];
+    const DevBlk blk = A.blks[bi];
+    const float scale = A.vbr_scale[bi];
+    const int nkt = (blk.nc + kTileK - 1) / kTileK;
+    const uint16_t *atiles = A.vbr_bf16 + blk.bf_off + (size_t)t * nkt * (kTileM * kTileK);
+    bool ok = true;
+    for (int kt = 0; kt < nkt && ok; ++kt) {
+      // A tile by TMA bulk copy
+      if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&S.bar_a)),
+                     "r"((unsigned)kTileBytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                su32(S.a)),
+            "l"(atiles + (size_t)kt * (kTileM * kTileK)), "r"((unsigned)kTileBytes), "r"(su32(&S.bar_a))
+            : "memory");
+      }
+      // B slice: rows k of B (K dim), columns n (N dim) -> bf16, K-major core matrices
+      const int kb = blk.c0 + kt * kTileK;
+      const int kvalid = min(kTileK, blk.c0 + blk.nc - kb);
+      {
+        const int n = tid;                       // one column of the tile per thread
+        const bool ncol = n0 + n < N;
+        const float *bp = B + (size_t)kb * ldb + n0 + n;
+#pragma unroll 2
+        for (int k8 = 0; k8 < kTileK / 8; ++k8) {
+          uint32_t w[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const int ka = 8 * k8 + 2 * h, kb2 = ka + 1;
+            const float f0 = (ncol && ka < kvalid) ? __ldg(bp + (size_t)ka * ldb) : 0.f;
+            const float f1 = (ncol && kb2 < kvalid) ? __ldg(bp + (size_t)kb2 * ldb) : 0.f;
+            const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(f0));
+            const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(f1));
+            w[h] = lo | (hi << 16);
+          }
+          *reinterpret_cast<uint4 *>(S.b + (n >> 3) * 1024 + k8 * 128 + (n & 7) * 16) =
+              make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        if (!bar_wait(&S.bar_a, ph_a)) {
+          atomicExch(A.err, (int)SABLE_ERR_TIMEOUT);
+          S.dead = 1;
+        } else {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int ks = 0; ks < kTileK / 16; ++ks) {
+            const uint64_t ad = smem_desc(S.a + ks * 256, 128, 1024);
+            const uint64_t bd = smem_desc(S.b + ks * 256, 128, 1024);
+            const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           su32(&S.bar_mma))
+                       : "memory");
+        }
+      }
+      ph_a ^= 1u;
+      __syncthreads();
+      if (S.dead) {
+        ok = false;
+        break;
+      }
+      // the tiles are overwritten next step: wait for the MMAs to finish reading them
+      const bool done = __all_sync(0xffffffffu, bar_wait(&S.bar_mma, ph_m));
+      ph_m ^= 1u;
+      if (!done) {
+        if (lane == 0) atomicExch(A.err, (int)SABLE_ERR_TIMEOUT);
+        S.dead = 1;
+      }
+      __syncthreads();
+      if (S.dead) ok = false;
+    }
+    if (!ok) break;
+    // epilogue: TMEM -> registers -> scale -> C
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = t * kTileM + 32 * warp + lane;          // row within the block
+    const bool rvalid = row < blk.nr;
+    float *crow = C + (size_t)(blk.r0 + (rvalid ? row : 0)) * ldc + n0;
+#pragma unroll 1
+    for (int ch = 0; ch < kTileN / 32; ++ch) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * ch);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (rvalid) {
+        const int cb = 32 * ch;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (n0 + cb + j < N) crow[cb + j] = __uint_as_float(r[j]) * scale;
+      }
+    }
+    // all warps have read the accumulator before the next job overwrites it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace
+
+size_t tc_smem_bytes() { return sizeof(TcShared) + 1024; }
+
+// Host: bf16 of a float, round to nearest even (NaN kept quiet).
+static uint16_t to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) return (uint16_t)((u >> 16) | 0x40);
+  const uint32_t r = u + 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(r >> 16);
+}
+
+// Host: power-of-two scale 2^ceil(log2 amax) (1 for an all-zero block).
+static float pow2_scale(float amax) {
+  if (!(amax > 0.f) || !std::isfinite(amax)) return 1.f;
+  int e;
+  const float m = std::frexp(amax, &e);   // amax = m 2^e, m in [0.5, 1)
+  return std::ldexp(1.f, m == 0.5f ? e - 1 : e);
+}
+
+void pack_vbr_bf16(const std::vector<Block> &blks, const std::vector<float> &canon,
+                   std::vector<uint16_t> &packed, std::vector<float> &scales, std::vector<int64_t> &offs) {
+  packed.clear();
+  scales.clear();
+  offs.clear();
+  int64_t voff = 0;
+  for (const Block &b : blks) {
+    float amax = 0.f;
+    for (int64_t k = 0; k < b.nr * b.nc; ++k) amax = std::max(amax, std::fabs(canon[voff + k]));
+    const float s = pow2_scale(amax);
+    scales.push_back(s);
+    offs.push_back((int64_t)packed.size());
+    const int64_t nt = (b.nr + kTileM - 1) / kTileM, nkt = (b.nc + kTileK - 1) / kTileK;
+    const size_t base = packed.size();
+    packed.resize(base + (size_t)(nt * nkt * kTileM * kTileK), 0);
+    for (int64_t t = 0; t < nt; ++t)
+      for (int64_t kt = 0; kt < nkt; ++kt) {
+        uint16_t *tile = packed.data() + base + (size_t)((t * nkt + kt) * kTileM * kTileK);
+        for (int m = 0; m < kTileM; ++m) {
+          const int64_t r = t * kTileM + m;
+          if (r >= b.nr) break;
+          for (int k = 0; k < kTileK; ++k) {
+            const int64_t c = kt * kTileK + k;
+            if (c >= b.nc) break;
+            const float v = canon[voff + c * b.nr + r] / s;     // exact: s is a power of two
+            tile[(m >> 3) * 512 + (k >> 3) * 64 + (m & 7) * 8 + (k & 7)] = to_bf16(v);
+          }
+        }
+      }
+    voff += b.nr * b.nc;
+  }
+}
+
+void vbr_tc_pairs(const std::vector<Block> &blks, std::vector<int32_t> &pairs) {
+  pairs.clear();
+  for (size_t bi = 0; bi < blks.size(); ++bi) {
+    const int64_t nt = (blks[bi].nr + kTileM - 1) / kTileM;
+    for (int64_t t = 0; t < nt; ++t) {
+      pairs.push_back((int32_t)bi);
+      pairs.push_back((int32_t)t);
+    }
+  }
+}
+
+sable_status launch_vbr_tc(sable_plan_t P, const DevHybrid &D, const float *B, int64_t ldb, float *C, int64_t ldc,
+                           int N, cudaStream_t_ st) {
+  const int ntn = (N + kTileN - 1) / kTileN;
+  const long long nj = (long long)D.n_tc_pairs * ntn;
+  if (nj == 0) return SABLE_OK;
+  if (nj > INT32_MAX) return SABLE_ERR_INVALID;
+  const int n_jobs = (int)nj;
+  const size_t smem = tc_smem_bytes();
+  // at most 4 CTAs per SM so that their TMEM allocations (128 columns each) fit
+  const size_t smem_req = std::max(smem, (size_t)56 * 1024);
+  cudaFuncSetAttribute(vbr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
+  const int grid = std::max(1, std::min(n_jobs, 4 * std::max(P->sm_count, 1)));
+  vbr_tc_kernel<<<grid, kTcThreads, smem_req, st>>>(D, n_jobs, ntn, B, ldb, C, ldc, N);
+  if (cudaGetLastError() != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(P, SABLE_ERR_CUDA);
+  }
+  return SABLE_OK;
+}
+
+}  // namespace sable

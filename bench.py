@@ -41,6 +41,7 @@ def _args():
     ap.add_argument("--impl", default="sable", choices=["sable", "reference"])
     ap.add_argument("--workload", default="spmv1m", choices=["spmv1m", "spmv4096"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-spmm", action="store_true")
     return ap.parse_args()
 
 
@@ -186,6 +187,63 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def spmm_section(sable, torch, dev, stream, steps, timed, peak):
+    """SpMM C = A B on the 200k x 200k blocks + scatter workload, N = 128:
+    hybrid VBR+CSR in FP32 and with BF16 blocks on the tensor cores, against
+    the library's plain CSR SpMM and cuSPARSE (through torch).  One plan: its
+    arrays plus B and C (~0.4 GB per call) exceed L2."""
+    import synth
+    N = 128
+    A = synth.blocks_scatter_200k()
+    t0 = time.perf_counter()
+    P = sable.plan_from(A, [(sable.VBR, dict(a_min=256)), (sable.CSR, None)])
+    t_ex = time.perf_counter() - t0
+    info = P.info()
+    B = torch.from_numpy(synth.dense_operand(13, A["n"], N)).to(dev)
+    C = torch.empty(A["m"], N, device=dev)
+    flops = 2.0 * info["nnz"] * N
+
+    def nbytes(cell_bytes):
+        return (cell_bytes * info["vbr_cells"] + 8 * info["nnz_csr"] + 4 * (info["m"] + 1) +
+                4 * info["n"] * N + 4 * info["m"] * N)
+
+    k = max(3, min(steps, 30))
+    out = {"workload": "spmm-vbr+csr-200k: 200,000^2, blocks side U{16..256} density 0.8 on disjoint "
+                       "rows/cols (~40% of entries), uniform scatter, N=128, U[-1,1]",
+           "nnz": info["nnz"], "nnz_vbr": info["nnz_vbr"], "blocks": info["n_blocks"], "N": N,
+           "extract_s": round(t_ex, 2), "steps": k}
+    res = {}
+    for name, fn, cb in (("fp32", lambda i: P.spmm(B, C, sable.FP32, stream), 4),
+                         ("bf16_blocks", lambda i: P.spmm(B, C, sable.BF16_BLOCKS, stream), 2),
+                         ("plain_csr", lambda i: P.csr_spmm(B, C, stream), None)):
+        for _ in range(3):
+            fn(0)
+        ms = timed(fn, k)
+        nb = nbytes(cb) if cb else 8 * info["nnz"] + 4 * (info["m"] + 1) + 4 * info["n"] * N + 4 * info["m"] * N
+        res[name] = {"ms": ms, "GFLOP/s": flops / (ms * 1e-3) / 1e9, "GB/s": nb / (ms * 1e-3) / 1e9,
+                     "frac_hbm": nb / (ms * 1e-3) / 1e9 / peak}
+    try:
+        order = np.lexsort((A["col"], A["row"]))
+        crow = np.zeros(A["m"] + 1, dtype=np.int64)
+        np.add.at(crow, A["row"].astype(np.int64) + 1, 1)
+        Acs = torch.sparse_csr_tensor(torch.from_numpy(np.cumsum(crow)).to(dev),
+                                      torch.from_numpy(A["col"][order].astype(np.int64)).to(dev),
+                                      torch.from_numpy(A["val"][order]).to(dev), size=(A["m"], A["n"]))
+        for _ in range(3):
+            torch.sparse.mm(Acs, B)
+        ms = timed(lambda i: torch.sparse.mm(Acs, B), k)
+        res["cusparse_csr"] = {"ms": ms, "GFLOP/s": flops / (ms * 1e-3) / 1e9}
+        del Acs
+    except Exception:
+        res["cusparse_csr"] = None
+    out.update(res)
+    best_plain = min(res["plain_csr"]["ms"], (res["cusparse_csr"] or {"ms": float("inf")})["ms"])
+    out["vs_plain_csr_fp32"] = best_plain / res["fp32"]["ms"]
+    out["vs_plain_csr_bf16"] = best_plain / res["bf16_blocks"]["ms"]
+    P.close()
+    return out
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -289,6 +347,10 @@ def main():
 
     k_e2e = min(args.steps, 500)
     ms_e2e = timed(e2e, k_e2e)
+    spmm = None
+    if not args.no_spmm and ws == 1:
+        peak_hbm, _src = _peaks()
+        spmm = spmm_section(sable, torch, dev, stream, args.steps, timed, peak_hbm)
 
     # max over ranks
     def rank_max(v):
@@ -353,6 +415,7 @@ def main():
             "e2e": {"value": nbytes * ws / (ms_e2e * 1e-3) / 1e9, "unit": "GB/s",
                     "h2d_bytes_per_step": 4 * info["n"], "d2h_bytes_per_step": 4 * info["m"],
                     "ms_per_step": ms_e2e, "steps": k_e2e},
+            "spmm": spmm,
             "gpu_launches": args.steps,
             "clocks": clocks,
         }

@@ -174,3 +174,22 @@ def test_bands_powerlaw_1m_full_size():
     assert oracle.normwise_err(_spmv(P, x), ref) <= TOL_FP32
     assert oracle.normwise_err(_spmv(P, x, plain=True), ref) <= TOL_FP32
     P.close()
+
+
+@pytest.mark.slow
+def test_blocks_scatter_200k_full_size_sampled():
+    """Full-size SpMM (200k^2, ~30M entries, N=128) in FP32 and with BF16
+    blocks, checked on 3000 sampled rows of C against the FP64 oracle."""
+    A = synth.blocks_scatter_200k()
+    P = sable.plan_from(A, [(sable.VBR, dict(a_min=256)), (sable.CSR, None)])
+    assert P.info()["n_blocks"] > 700
+    B = synth.dense_operand(13, A["n"], 128)
+    sel = np.random.default_rng(0).choice(A["m"], 3000, replace=False)
+    ref = oracle.spmm_rows(A["m"], A["row"], A["col"], A["val"], B, sel)
+    Bd = _dev(B)
+    for prec, tol in ((sable.FP32, TOL_FP32), (sable.BF16_BLOCKS, 2e-2)):
+        C = torch.empty(A["m"], 128, device="cuda")
+        P.spmm(Bd, C, prec)
+        torch.cuda.synchronize()
+        assert oracle.normwise_err(C[torch.from_numpy(sel).cuda()].cpu().numpy(), ref) <= tol
+    P.close()

@@ -32,6 +32,8 @@ template <> struct VecT<4> {
   using T = float4;
   __device__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   __device__ static T load(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+  __device__ static T load_once(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
+  __device__ static void store_once(float *p, const T &a) { __stcs(reinterpret_cast<float4 *>(p), a); }
   __device__ static void fma(T &a, float s, const T &b) {
     a.x = fmaf(s, b.x, a.x); a.y = fmaf(s, b.y, a.y); a.z = fmaf(s, b.z, a.z); a.w = fmaf(s, b.w, a.w);
   }
@@ -46,6 +48,8 @@ template <> struct VecT<1> {
   using T = float;
   __device__ static T zero() { return 0.f; }
   __device__ static T load(const float *p) { return __ldg(p); }
+  __device__ static T load_once(const float *p) { return __ldcs(p); }
+  __device__ static void store_once(float *p, const T &a) { __stcs(p, a); }
   __device__ static void fma(T &a, float s, const T &b) { a = fmaf(s, b, a); }
   __device__ static void add_to(float *p, const T &a) { p[0] += a; }
   __device__ static void atomic_add_to(float *p, const T &a) { atomicAdd(p, a); }
@@ -90,7 +94,7 @@ spmm_hybrid_kernel(const DevHybrid A, const float *__restrict__ B, int64_t ldb, 
         for (int k = 0; k < s.ndiag; ++k) {
           const int c = r + s.off_lo + k;
           if ((unsigned)c >= n) continue;
-          const float v = __ldg(vp + (int64_t)k * s.ld);
+          const float v = __ldcs(vp + (int64_t)k * s.ld);
           if (lane_ok) Vt::fma(acc, v, Vt::load(B + (int64_t)c * ldb + n0 + lc));
         }
         if (lane_ok) Vt::add_to(cs + i * NT + lc, acc);
@@ -103,7 +107,7 @@ spmm_hybrid_kernel(const DevHybrid A, const float *__restrict__ B, int64_t ldb, 
         const int ia = max(r0, b.r0) - r0, ib = min(I.r1, b.r0 + b.nr) - r0;
         const int first = ia + ((warp - ia % NW) + NW) % NW;
         for (int i = first; i < ib; i += NW)
-          if (lane_ok) Vt::add_to(cs + i * NT + lc, Vt::load(C + (int64_t)(r0 + i) * ldc + n0 + lc));
+          if (lane_ok) Vt::add_to(cs + i * NT + lc, Vt::load_once(C + (int64_t)(r0 + i) * ldc + n0 + lc));
       }
     } else
     for (int q = I.blk_lo; q < I.blk_hi; ++q) {
@@ -154,8 +158,8 @@ spmm_hybrid_kernel(const DevHybrid A, const float *__restrict__ B, int64_t ldb, 
         float v = 0.f;
         int c = 0;
         if (p < pz) {
-          v = __ldg(A.cv + p);
-          c = __ldg(A.ci + p);
+          v = __ldcs(A.cv + p);
+          c = __ldcs(A.ci + p);
         }
         const int cnt = min(32, pz - base);
         for (int j = 0; j < cnt; j += 4) {
@@ -194,9 +198,9 @@ spmm_hybrid_kernel(const DevHybrid A, const float *__restrict__ B, int64_t ldb, 
         const float *src = cs + i * NT + lc;
         float *dst = C + (int64_t)(r0 + i) * ldc + n0 + lc;
         if (V == 4) {
-          *reinterpret_cast<float4 *>(dst) = *reinterpret_cast<const float4 *>(src);
+          __stcs(reinterpret_cast<float4 *>(dst), *reinterpret_cast<const float4 *>(src));
         } else {
-          dst[0] = src[0];
+          __stcs(dst, src[0]);
         }
       }
     }

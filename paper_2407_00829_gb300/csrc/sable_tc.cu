@@ -192,11 +192,11 @@ vbr_tc_kernel(const DevHybrid A, int n_jobs, int ntn, const float *__restrict__ 
       if (S.dead) ok = false;
     }
     if (!ok) break;
-    // epilogue: TMEM -> registers -> scale -> C
+    // epilogue: TMEM -> registers -> scale -> shared (transpose) -> C, whole
+    // rows per store instruction.  The A/B tiles are free: the MMAs are done.
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int row = t * kTileM + 32 * warp + lane;          // row within the block
-    const bool rvalid = row < blk.nr;
-    float *crow = C + (size_t)(blk.r0 + (rvalid ? row : 0)) * ldc + n0;
+    float *stage = reinterpret_cast<float *>(S.a) + warp * (32 * 33);   // 32 rows x 33 (padded)
+    const int rbase = t * kTileM + 32 * warp;                             // first row of my warp in the block
 #pragma unroll 1
     for (int ch = 0; ch < kTileN / 32; ++ch) {
       uint32_t r[32];
@@ -211,12 +211,16 @@ vbr_tc_kernel(const DevHybrid A, int n_jobs, int ntn, const float *__restrict__ 
             "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (rvalid) {
-        const int cb = 32 * ch;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (n0 + cb + j < N) crow[cb + j] = __uint_as_float(r[j]) * scale;
+      for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]) * scale;
+      __syncwarp();
+      const int col = n0 + 32 * ch + lane;
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const int row = rbase + rr;
+        if (row < blk.nr && col < N) C[(size_t)(blk.r0 + row) * ldc + col] = stage[rr * 33 + lane];
       }
+      __syncwarp();
     }
     // all warps have read the accumulator before the next job overwrites it
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

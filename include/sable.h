@@ -171,6 +171,40 @@ sable_status sable_plan_get_csr(sable_plan_t plan, int64_t *row_ptr, int32_t *co
 sable_status sable_plan_set_tiling(sable_plan_t plan, int32_t spmv_rows, int64_t spmv_bytes,
                                    int32_t spmm_rows, int64_t spmm_elems);
 
+/* ---- Batches: many matrices in one grouped launch per op ----------------
+ * A batch is built from `count` uploaded plans (same device; the plans must
+ * outlive the batch).  It concatenates their row-tile tables, each tile
+ * tagged with its matrix, so that one launch computes every region of every
+ * matrix.  Errors: SABLE_ERR_ORDER if a plan is not uploaded;
+ * SABLE_ERR_INVALID (NULL, other device, plan in error); SABLE_ERR_OOM. */
+sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_batch_t *out);
+
+/* y_i := A_i x_i for every matrix i of the batch, one launch.  x and y are
+ * DEVICE arrays of `count` device pointers (x_i: n_i floats, y_i: m_i floats). */
+sable_status sable_batch_spmv(sable_batch_t batch, const float *const *x, float *const *y, void *stream);
+
+/* C_i := A_i B_i, one launch (two with BF16 blocks).  B and C are DEVICE
+ * arrays of device pointers; B_i is n_i x N and C_i is m_i x N, row-major with
+ * leading dimension N; when N is a multiple of 4 every B_i and C_i must be
+ * 16-byte aligned. */
+sable_status sable_batch_spmm(sable_batch_t batch, const float *const *B, int64_t N, float *const *C,
+                              sable_precision prec, void *stream);
+
+/* Capture the batch's SpMV / SpMM launches (with these operand tables) into a
+ * CUDA graph; sable_graph_launch replays it on a stream.  The operand tables
+ * and the buffers they point to are read at every replay. */
+typedef struct sable_graph_s *sable_graph_t;
+sable_status sable_batch_graph_spmv(sable_batch_t batch, const float *const *x, float *const *y,
+                                    sable_graph_t *out);
+sable_status sable_batch_graph_spmm(sable_batch_t batch, const float *const *B, int64_t N, float *const *C,
+                                    sable_precision prec, sable_graph_t *out);
+sable_status sable_graph_launch(sable_graph_t graph, void *stream);
+sable_status sable_graph_destroy(sable_graph_t graph);
+
+/* Device error word of the batch (0, or a sable_status recorded by a kernel). */
+sable_status sable_batch_status(sable_batch_t batch, int32_t *device_error);
+sable_status sable_batch_destroy(sable_batch_t batch);
+
 /* Calibration: `count` random 4-byte reads of x[0..n) (device), indices from a
  * fixed hash reduced modulo n, one kernel launch on `stream`; `out` (device,
  * one float) may be written.  Timing it gives the device's rate of random

@@ -29,7 +29,9 @@ EXPORTED = [
     "sable_plan_info", "sable_plan_get_segments", "sable_plan_get_blocks",
     "sable_plan_get_vdia_values", "sable_plan_get_vbr_values", "sable_plan_get_csr",
     "sable_plan_set_tiling", "sable_plan_status", "sable_plan_destroy", "sable_status_string",
-    "sable_probe_gather",
+    "sable_probe_gather", "sable_batch_create", "sable_batch_spmv", "sable_batch_spmm",
+    "sable_batch_graph_spmv", "sable_batch_graph_spmm", "sable_graph_launch", "sable_graph_destroy",
+    "sable_batch_status", "sable_batch_destroy",
 ]
 
 
@@ -85,6 +87,15 @@ def lib():
             "sable_plan_destroy": ([p], i32),
             "sable_status_string": ([i32], ctypes.c_char_p),
             "sable_probe_gather": ([p, i64, i64, p, p], i32),
+            "sable_batch_create": ([p, i32, p], i32),
+            "sable_batch_spmv": ([p, p, p, p], i32),
+            "sable_batch_spmm": ([p, p, i64, p, i32, p], i32),
+            "sable_batch_graph_spmv": ([p, p, p, p], i32),
+            "sable_batch_graph_spmm": ([p, p, i64, p, i32, p], i32),
+            "sable_graph_launch": ([p, p], i32),
+            "sable_graph_destroy": ([p], i32),
+            "sable_batch_status": ([p, p], i32),
+            "sable_batch_destroy": ([p], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -242,6 +253,90 @@ def probe_gather(x, count: int, out, stream=None):
     """Launch the random-gather calibration kernel (see include/sable.h)."""
     _check(lib().sable_probe_gather(_dptr(x), x.numel(), int(count), _dptr(out), _stream_handle(stream)),
            "sable_probe_gather")
+
+
+class Graph:
+    """A captured CUDA graph of batch launches (keeps its operand tables alive)."""
+
+    def __init__(self, handle, keep):
+        self._h, self._keep = handle, keep
+
+    def launch(self, stream=None):
+        _check(lib().sable_graph_launch(self._h, _stream_handle(stream)), "sable_graph_launch")
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().sable_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many uploaded plans computed by one grouped launch per op."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * max(1, len(self.plans)))(*[P.handle for P in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib().sable_batch_create(arr, len(self.plans), ctypes.byref(h)), "sable_batch_create")
+        self._h = h
+
+    @staticmethod
+    def _ptrs(tensors):
+        import torch
+        dev = tensors[0].device if tensors else torch.device("cuda")
+        return torch.tensor([t.data_ptr() for t in tensors] or [0], dtype=torch.int64, device=dev)
+
+    def spmv(self, xs, ys, stream=None):
+        px, py = self._ptrs(xs), self._ptrs(ys)
+        _check(lib().sable_batch_spmv(self._h, px.data_ptr(), py.data_ptr(), _stream_handle(stream)),
+               "sable_batch_spmv")
+        return (px, py)
+
+    def spmm(self, Bs, Cs, N, precision=FP32, stream=None):
+        pb, pc = self._ptrs(Bs), self._ptrs(Cs)
+        _check(lib().sable_batch_spmm(self._h, pb.data_ptr(), int(N), pc.data_ptr(), precision,
+                                      _stream_handle(stream)), "sable_batch_spmm")
+        return (pb, pc)
+
+    def graph_spmv(self, xs, ys) -> Graph:
+        px, py = self._ptrs(xs), self._ptrs(ys)
+        import torch
+        torch.cuda.synchronize()
+        g = ctypes.c_void_p()
+        _check(lib().sable_batch_graph_spmv(self._h, px.data_ptr(), py.data_ptr(), ctypes.byref(g)),
+               "sable_batch_graph_spmv")
+        return Graph(g, (px, py, xs, ys))
+
+    def graph_spmm(self, Bs, Cs, N, precision=FP32) -> Graph:
+        pb, pc = self._ptrs(Bs), self._ptrs(Cs)
+        import torch
+        torch.cuda.synchronize()
+        g = ctypes.c_void_p()
+        _check(lib().sable_batch_graph_spmm(self._h, pb.data_ptr(), int(N), pc.data_ptr(), precision,
+                                            ctypes.byref(g)), "sable_batch_graph_spmm")
+        return Graph(g, (pb, pc, Bs, Cs))
+
+    def device_error(self) -> int:
+        v = ctypes.c_int32()
+        _check(lib().sable_batch_status(self._h, ctypes.byref(v)), "sable_batch_status")
+        return v.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sable_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def plan_from(A: dict, extractors, tiling: Optional[dict] = None, upload: bool = True, stream=None) -> Plan:

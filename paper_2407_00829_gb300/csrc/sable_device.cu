@@ -58,25 +58,19 @@ template <> struct VecT<1> {
 // C[:, n0:n0+NT] for every item; V = 4 needs N, ldb, ldc multiples of 4 and
 // 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
 template <int THREADS, int V, bool VBRC>
-__global__ void __launch_bounds__(THREADS)
-spmm_hybrid_kernel(const DevHybrid A, const float *__restrict__ B, int64_t ldb, float *__restrict__ C,
-                   int64_t ldc, int N) {
+__device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, const float *__restrict__ B,
+                                          int64_t ldb, float *__restrict__ C, int64_t ldc, int N, float *cs,
+                                          int *rps) {
   using Vt = VecT<V>;
   using T = typename Vt::T;
   constexpr int NT = 32 * V;
   constexpr int NW = THREADS / 32;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int rows_max = A.spmm.rows_max;
-  float *cs = reinterpret_cast<float *>(smem_raw);
-  int *rps = reinterpret_cast<int *>(cs + rows_max * NT);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n0 = blockIdx.y * NT;
   const int lc = V * lane;                       // this lane's first column in the tile
   const bool lane_ok = n0 + lc < N;
   const unsigned n = (unsigned)A.n;
-
-  for (int it = blockIdx.x; it < A.spmm.n; it += gridDim.x) {
-    const DevItem I = A.spmm.items[it];
+  {
     const int r0 = I.r0, R = I.r1 - I.r0;
     for (int i = tid; i < R * NT; i += THREADS) cs[i] = 0.f;
     for (int i = tid; i <= R; i += THREADS) rps[i] = __ldg(A.rp + r0 + i);
@@ -205,6 +199,36 @@ spmm_hybrid_kernel(const DevHybrid A, const float *__restrict__ B, int64_t ldb, 
       }
     }
     __syncthreads();
+  }
+}
+
+// C[:, n0:n0+NT] of one matrix; V = 4 needs N, ldb, ldc multiples of 4 and
+// 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
+template <int THREADS, int V, bool VBRC>
+__global__ void __launch_bounds__(THREADS)
+spmm_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ B, int64_t ldb,
+                   float *__restrict__ C, int64_t ldc, int N) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *cs = reinterpret_cast<float *>(smem_raw);
+  int *rps = reinterpret_cast<int *>(cs + A.spmm.rows_max * 32 * V);
+  for (int it = blockIdx.x; it < A.spmm.n; it += gridDim.x) {
+    const DevItem I = A.spmm.items[it];
+    spmm_tile<THREADS, V, VBRC>(A, I, B, ldb, C, ldc, N, cs, rps);
+  }
+}
+
+// Many matrices in one launch (B_i: n_i x N, C_i: m_i x N, both with leading
+// dimension N).
+template <int THREADS, int V, bool VBRC>
+__global__ void __launch_bounds__(THREADS)
+spmm_grouped_kernel(const DevHybrid *__restrict__ mats, const DevItem *__restrict__ items, int n_items,
+                    int rows_max, const float *const *__restrict__ Bs, float *const *__restrict__ Cs, int N) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *cs = reinterpret_cast<float *>(smem_raw);
+  int *rps = reinterpret_cast<int *>(cs + rows_max * 32 * V);
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const DevItem I = items[it];
+    spmm_tile<THREADS, V, VBRC>(mats[I.mat], I, Bs[I.mat], N, Cs[I.mat], N, N, cs, rps);
   }
 }
 
@@ -379,7 +403,8 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
       std::vector<int64_t> offs;
       pack_vbr_bf16(H.blks, H.vbr_canon, S->vbr_bf16, S->vbr_scale, offs);
       for (size_t b = 0; b < S->blks.size(); ++b) S->blks[b].bf_off = offs[b];
-      vbr_tc_pairs(H.blks, S->tc_pairs);
+      S->tc_pairs.clear();
+      vbr_tc_pairs(H.blks, 0, S->tc_pairs);
     }
     S->rp.assign(H.crp.begin(), H.crp.end());
     S->ci.assign(H.cci.begin(), H.cci.end());
@@ -412,6 +437,7 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   const size_t o_bf16 = ar.add(S->vbr_bf16.data(), vec_bytes(S->vbr_bf16));
   const size_t o_scale = ar.add(S->vbr_scale.data(), vec_bytes(S->vbr_scale));
   const size_t o_pairs = ar.add(S->tc_pairs.data(), vec_bytes(S->tc_pairs));
+  const size_t o_self = ar.reserve(sizeof(DevHybrid));
   const size_t o_rp = ar.add(S->rp.data(), vec_bytes(S->rp));
   const size_t o_ci = ar.add(S->ci.data(), vec_bytes(S->ci));
   const size_t o_cv = ar.add(S->cv.data(), vec_bytes(S->cv));
@@ -465,8 +491,9 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   D.vbr = reinterpret_cast<const float *>(blob + o_vbr);
   D.vbr_bf16 = reinterpret_cast<const uint16_t *>(blob + o_bf16);
   D.vbr_scale = reinterpret_cast<const float *>(blob + o_scale);
-  D.tc_pairs = reinterpret_cast<const int32_t *>(blob + o_pairs);
-  D.n_tc_pairs = (int32_t)(S->tc_pairs.size() / 2);
+  D.n_tc = (int32_t)(S->tc_pairs.size() / 3);
+  P->dev_trip = reinterpret_cast<const int32_t *>(blob + o_pairs);
+  P->dev_self = reinterpret_cast<DevHybrid *>(blob + o_self);
   D.rp = reinterpret_cast<const int32_t *>(blob + o_rp);
   D.ci = reinterpret_cast<const int32_t *>(blob + o_ci);
   D.cv = reinterpret_cast<const float *>(blob + o_cv);
@@ -484,7 +511,16 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   Q.spmv = items_of(2, its[2]);
   Q.spmm = items_of(3, its[3]);
   P->stats.n_items = D.spmv.n;
+  P->h_items_v = S->it_v.items;
+  P->h_items_m = S->it_m.items;
+  P->h_trip = S->tc_pairs;
   delete S;
+  e = cudaMemcpy(P->dev_self, &P->dev, sizeof(DevHybrid), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(blob);
+    P->dev_blob = nullptr;
+    return cuda_fail(P, e);
+  }
   P->dev_blob = blob;
   P->dev_bytes = ar.off;
   P->device = dev;
@@ -576,11 +612,12 @@ sable_status sable_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, 
   const sable_status s = check_ready(P);
   if (s) return s;
   if (prec != SABLE_FP32 && prec != SABLE_BF16_BLOCKS) return SABLE_ERR_INVALID;
-  const bool bf16 = prec == SABLE_BF16_BLOCKS && P->dev.n_tc_pairs > 0;
+  const bool bf16 = prec == SABLE_BF16_BLOCKS && P->dev.n_tc > 0;
   if (bf16) {
-    if (N < 1 || ldb < N || ldc < N || !B || !C) return SABLE_ERR_INVALID;
-    const sable_status s2 = launch_vbr_tc(P, P->dev, B, ldb, C, ldc, (int)N, (cudaStream_t)stream);
-    if (s2) return s2;
+    if (N < 1 || ldb < N || ldc < N || !B || !C || N > INT32_MAX) return SABLE_ERR_INVALID;
+    const sable_status s2 = launch_vbr_tc(P->dev_self, P->dev_trip, P->dev.n_tc, B, ldb, C, ldc, nullptr, nullptr,
+                                          (int)N, P->sm_count, P->dev.err, (cudaStream_t)stream);
+    if (s2) return fail(P, s2);
   }
   return launch_spmm(P, P->dev, B, N, ldb, C, ldc, bf16, (cudaStream_t)stream);
 }
@@ -607,3 +644,32 @@ sable_status sable_plan_destroy(sable_plan_t P) {
 }
 
 }  // extern "C"
+
+namespace sable {
+
+sable_status launch_spmm_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,
+                                 const float *const *Bs, float *const *Cs, int N, bool vbrc, int sm_count,
+                                 cudaStream_t_ st) {
+  if (n_items == 0) return SABLE_OK;
+  constexpr int TH = 256;
+  const bool vec = N % 4 == 0;   // B_i, C_i must then be 16-byte aligned (documented)
+  const int NT = vec ? 128 : 32;
+  const size_t smem = (size_t)rows_max * NT * 4 + ((size_t)rows_max + 1) * 4;
+  const int gy = (N + NT - 1) / NT;
+  auto go = [&](auto k) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(grid_for(k, TH, smem, n_items, sm_count), gy);
+    k<<<grid, TH, smem, st>>>(mats, items, n_items, rows_max, Bs, Cs, N);
+  };
+  if (vec && vbrc) go(spmm_grouped_kernel<TH, 4, true>);
+  else if (vbrc) go(spmm_grouped_kernel<TH, 1, true>);
+  else if (vec) go(spmm_grouped_kernel<TH, 4, false>);
+  else go(spmm_grouped_kernel<TH, 1, false>);
+  if (cudaGetLastError() != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SABLE_ERR_CUDA;
+  }
+  return SABLE_OK;
+}
+
+}  // namespace sable

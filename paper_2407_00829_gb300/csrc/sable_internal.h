@@ -83,8 +83,7 @@ struct DevHybrid {
   const float *vbr = nullptr;
   const uint16_t *vbr_bf16 = nullptr;
   const float *vbr_scale = nullptr;  // per block power-of-two scale
-  const int32_t *tc_pairs = nullptr; // (block, 128-row tile) pairs for the tensor-core path
-  int32_t n_tc_pairs = 0;
+  int32_t n_tc = 0;                  // (block, 128-row tile) pairs for the tensor-core path
   const int32_t *rp = nullptr;   // CSR remainder row pointer (m + 1)
   const int32_t *ci = nullptr;   // padded by kCsrPad entries
   const float *cv = nullptr;     // padded by kCsrPad entries
@@ -135,6 +134,10 @@ struct sable_plan_s {
   void *dev_blob = nullptr;            // one allocation holding every table
   size_t dev_bytes = 0;
   sable::DevHybrid dev;                // hybrid tables
+  sable::DevHybrid *dev_self = nullptr;// device copy of `dev` (matrix table of one entry)
+  const int32_t *dev_trip = nullptr;   // (0, block, row tile) triples for the tensor-core path
+  std::vector<sable::DevItem> h_items_v, h_items_m;   // host copies of the tile tables
+  std::vector<int32_t> h_trip;
   sable::DevHybrid dev_plain;          // whole matrix as CSR (comparison kernel)
   int32_t *dev_err = nullptr;
   int device = -1;
@@ -157,9 +160,15 @@ int host_threads();
 // sable_tc.cu: BF16 VBR blocks on the tensor cores
 void pack_vbr_bf16(const std::vector<Block> &blks, const std::vector<float> &canon,
                    std::vector<uint16_t> &packed, std::vector<float> &scales, std::vector<int64_t> &offs);
-void vbr_tc_pairs(const std::vector<Block> &blks, std::vector<int32_t> &pairs);
-sable_status launch_vbr_tc(sable_plan_t P, const DevHybrid &D, const float *B, int64_t ldb, float *C, int64_t ldc,
-                           int N, cudaStream_t_ st);
+void vbr_tc_pairs(const std::vector<Block> &blks, int32_t mat, std::vector<int32_t> &trip);
+sable_status launch_vbr_tc(const DevHybrid *mats, const int32_t *trip, int n_trip, const float *B, int64_t ldb,
+                           float *C, int64_t ldc, const float *const *Bs, float *const *Cs, int N, int sm_count,
+                           int *err, cudaStream_t_ st);
+sable_status launch_spmv_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,
+                                 const float *const *xs, float *const *ys, int sm_count, cudaStream_t_ st);
+sable_status launch_spmm_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,
+                                 const float *const *Bs, float *const *Cs, int N, bool vbrc, int sm_count,
+                                 cudaStream_t_ st);
 // sable_spmv.cu
 sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const float *x, float *y,
                          cudaStream_t_ st);

@@ -32,19 +32,13 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
 
 template <bool PLAIN>
-__global__ void __launch_bounds__(kThreads, 8)
-spmv_hybrid_kernel(const DevHybrid A, const float *__restrict__ x, float *__restrict__ y) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const DevItems &T = A.spmv;
-  const int rows_max = T.rows_max;
-  float *ys = reinterpret_cast<float *>(smem_raw);
-  int *rps = reinterpret_cast<int *>(ys + rows_max);
+__device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T, const DevItem &I,
+                                          const float *__restrict__ x, float *__restrict__ y, float *ys,
+                                          int *rps) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kThreads / 32;
   const unsigned n = (unsigned)A.n;
-
-  for (int it = blockIdx.x; it < T.n; it += gridDim.x) {
-    const DevItem I = T.items[it];
+  {
     const int r0 = I.r0, R = I.r1 - I.r0;
     for (int i = tid; i <= R; i += kThreads) rps[i] = __ldg(A.rp + r0 + i);
 
@@ -148,6 +142,34 @@ spmv_hybrid_kernel(const DevHybrid A, const float *__restrict__ x, float *__rest
   }
 }
 
+// One matrix: tiles A.spmv.items[blockIdx.x + k gridDim.x].
+template <bool PLAIN>
+__global__ void __launch_bounds__(kThreads, 8)
+spmv_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ x, float *__restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *ys = reinterpret_cast<float *>(smem_raw);
+  int *rps = reinterpret_cast<int *>(ys + A.spmv.rows_max);
+  for (int it = blockIdx.x; it < A.spmv.n; it += gridDim.x) {
+    const DevItem I = A.spmv.items[it];
+    spmv_tile<PLAIN>(A, A.spmv, I, x, y, ys, rps);
+  }
+}
+
+// Many matrices in one launch: the grouped tile table carries each tile's
+// matrix index; xs / ys hold one device pointer per matrix.
+__global__ void __launch_bounds__(kThreads, 8)
+spmv_grouped_kernel(const DevHybrid *__restrict__ mats, const DevItem *__restrict__ items, int n_items,
+                    int rows_max, const float *const *__restrict__ xs, float *const *__restrict__ yv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *ys = reinterpret_cast<float *>(smem_raw);
+  int *rps = reinterpret_cast<int *>(ys + rows_max);
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const DevItem I = items[it];
+    const DevHybrid &A = mats[I.mat];
+    spmv_tile<false>(A, A.spmv, I, xs[I.mat], yv[I.mat], ys, rps);
+  }
+}
+
 sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const float *x, float *y,
                          cudaStream_t_ st) {
   if (D.m == 0) return SABLE_OK;
@@ -163,6 +185,28 @@ sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const f
   if (cudaGetLastError() != cudaSuccess) {
     (void)cudaGetLastError();
     return fail(P, SABLE_ERR_CUDA);
+  }
+  return SABLE_OK;
+}
+
+}  // namespace sable
+
+namespace sable {
+
+sable_status launch_spmv_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,
+                                 const float *const *xs, float *const *ys, int sm_count, cudaStream_t_ st) {
+  if (n_items == 0) return SABLE_OK;
+  if (rows_max > 4 * kThreads) return SABLE_ERR_INVALID;
+  const size_t smem = (size_t)rows_max * 4 + ((size_t)rows_max + 1) * 4;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmv_grouped_kernel, kThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int grid = std::max(1, std::min(n_items, per_sm * std::max(sm_count, 1)));
+  spmv_grouped_kernel<<<grid, kThreads, smem, st>>>(mats, items, n_items, rows_max, xs, ys);
+  if (cudaGetLastError() != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SABLE_ERR_CUDA;
   }
   return SABLE_OK;
 }

@@ -84,8 +84,9 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTi
                             ((uint32_t)(kTileM >> 4) << 24);
 
 __global__ void __launch_bounds__(kTcThreads, 1)
-vbr_tc_kernel(const DevHybrid A, int n_jobs, int ntn, const float *__restrict__ B, int64_t ldb,
-              float *__restrict__ C, int64_t ldc, int N) {
+vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ trip, int n_jobs, int ntn,
+              const float *B0, int64_t ldb0, float *C0, int64_t ldc0, const float *const *Bs, float *const *Cs,
+              int N, int *err) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   // align the working area to 1024 bytes
   TcShared &S = *reinterpret_cast<TcShared *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -110,7 +111,11 @@ vbr_tc_kernel(const DevHybrid A, int n_jobs, int ntn, const float *__restrict__ 
 
   for (int job = blockIdx.x; job < n_jobs; job += gridDim.x) {
     const int pair = job / ntn, n0 = (job - pair * ntn) * kTileN;
-    const int bi = A.tc_pairs[2 * pair], t = A.tc_pairs[2 * pair + 1];
+    const int mat = trip[3 * pair], bi = trip[3 * pair + 1], t = trip[3 * pair + 2];
+    const DevHybrid &A = mats[mat];
+    const float *__restrict__ B = Bs ? Bs[mat] : B0;
+    float *__restrict__ C = Cs ? Cs[mat] : C0;
+    const int64_t ldb = Bs ? N : ldb0, ldc = Cs ? N : ldc0;
     const DevBlk blk = A.blks[bi];
     const float scale = A.vbr_scale[bi];
     const int nkt = (blk.nc + kTileK - 1) / kTileK;
@@ -155,7 +160,7 @@ vbr_tc_kernel(const DevHybrid A, int n_jobs, int ntn, const float *__restrict__ 
       __syncthreads();
       if (tid == 0) {
         if (!bar_wait(&S.bar_a, ph_a)) {
-          atomicExch(A.err, (int)SABLE_ERR_TIMEOUT);
+          atomicExch(err, (int)SABLE_ERR_TIMEOUT);
           S.dead = 1;
         } else {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -185,7 +190,7 @@ vbr_tc_kernel(const DevHybrid A, int n_jobs, int ntn, const float *__restrict__ 
       const bool done = __all_sync(0xffffffffu, bar_wait(&S.bar_mma, ph_m));
       ph_m ^= 1u;
       if (!done) {
-        if (lane == 0) atomicExch(A.err, (int)SABLE_ERR_TIMEOUT);
+        if (lane == 0) atomicExch(err, (int)SABLE_ERR_TIMEOUT);
         S.dead = 1;
       }
       __syncthreads();
@@ -287,33 +292,33 @@ void pack_vbr_bf16(const std::vector<Block> &blks, const std::vector<float> &can
   }
 }
 
-void vbr_tc_pairs(const std::vector<Block> &blks, std::vector<int32_t> &pairs) {
-  pairs.clear();
+void vbr_tc_pairs(const std::vector<Block> &blks, int32_t mat, std::vector<int32_t> &trip) {
   for (size_t bi = 0; bi < blks.size(); ++bi) {
     const int64_t nt = (blks[bi].nr + kTileM - 1) / kTileM;
     for (int64_t t = 0; t < nt; ++t) {
-      pairs.push_back((int32_t)bi);
-      pairs.push_back((int32_t)t);
+      trip.push_back(mat);
+      trip.push_back((int32_t)bi);
+      trip.push_back((int32_t)t);
     }
   }
 }
 
-sable_status launch_vbr_tc(sable_plan_t P, const DevHybrid &D, const float *B, int64_t ldb, float *C, int64_t ldc,
-                           int N, cudaStream_t_ st) {
+sable_status launch_vbr_tc(const DevHybrid *mats, const int32_t *trip, int n_trip, const float *B, int64_t ldb,
+                           float *C, int64_t ldc, const float *const *Bs, float *const *Cs, int N, int sm_count,
+                           int *err, cudaStream_t_ st) {
   const int ntn = (N + kTileN - 1) / kTileN;
-  const long long nj = (long long)D.n_tc_pairs * ntn;
+  const long long nj = (long long)n_trip * ntn;
   if (nj == 0) return SABLE_OK;
   if (nj > INT32_MAX) return SABLE_ERR_INVALID;
-  const int n_jobs = (int)nj;
   const size_t smem = tc_smem_bytes();
   // at most 4 CTAs per SM so that their TMEM allocations (128 columns each) fit
   const size_t smem_req = std::max(smem, (size_t)56 * 1024);
   cudaFuncSetAttribute(vbr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
-  const int grid = std::max(1, std::min(n_jobs, 4 * std::max(P->sm_count, 1)));
-  vbr_tc_kernel<<<grid, kTcThreads, smem_req, st>>>(D, n_jobs, ntn, B, ldb, C, ldc, N);
+  const int grid = std::max(1, std::min((int)nj, 4 * std::max(sm_count, 1)));
+  vbr_tc_kernel<<<grid, kTcThreads, smem_req, st>>>(mats, trip, (int)nj, ntn, B, ldb, C, ldc, Bs, Cs, N, err);
   if (cudaGetLastError() != cudaSuccess) {
     (void)cudaGetLastError();
-    return fail(P, SABLE_ERR_CUDA);
+    return SABLE_ERR_CUDA;
   }
   return SABLE_OK;
 }

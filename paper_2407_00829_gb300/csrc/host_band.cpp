@@ -99,9 +99,11 @@ std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p) 
   const int64_t d_max = p.d_max > 0 ? p.d_max : std::max(m, n);
   const int64_t count_min =
       p.count_min > 0 ? p.count_min : (int64_t)std::ceil(p.delta * (double)p.l_seg);
-  // M[d] over the offset range [-(m-1), n-1]
+  // M[d] over the offset range [-(m-1), n-1], and for every offset the rows
+  // holding a residual entry on it (ascending): FitRibbon(i, d) is (0, 0, 0)
+  // for every other row, so only these rows are visited.
   const int64_t span = m + n;
-  std::vector<int64_t> M(span > 0 ? span : 1, 0);
+  std::vector<int64_t> M(span > 0 ? span + 1 : 1, 0);
   for (int64_t i = 0; i < m; ++i)
     for (int64_t k = R.rp[i]; k < R.rp[i + 1]; ++k) {
       const int64_t d = (int64_t)R.ci[k] - i;
@@ -114,29 +116,45 @@ std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p) 
     if (M[a + m] != M[b + m]) return M[a + m] > M[b + m];
     return a < b;
   });
+  std::vector<int64_t> start(span + 1, 0);
+  for (int64_t t = 0; t < span; ++t) start[t + 1] = start[t] + M[t];
+  std::vector<int32_t> drow(start[span]);
+  {
+    std::vector<int64_t> pos(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t k = R.rp[i]; k < R.rp[i + 1]; ++k) {
+        const int64_t d = (int64_t)R.ci[k] - i;
+        if (d <= d_max && -d <= d_max) drow[pos[d + m]++] = (int32_t)i;
+      }
+  }
 
   std::vector<uint8_t> used(m, 0);
-  std::vector<Ext> ext(m);
+  std::vector<Ext> ext;
   std::vector<BandSeg> out;
   for (const int64_t d : D) {
-    parallel_rows(m, [&](int64_t a, int64_t b) {
-      for (int64_t i = a; i < b; ++i)
-        ext[i] = used[i] ? Ext{0, 0, 0} : fit_ribbon(R, i, d, p.delta, p.w_max);
-    });
-    // GrowSegments (Algorithm 4)
+    const int32_t *rows = drow.data() + start[d + m];
+    const int64_t len = M[d + m];
+    ext.resize(len);
+    auto fit = [&](int64_t a, int64_t b) {
+      for (int64_t t = a; t < b; ++t)
+        ext[t] = used[rows[t]] ? Ext{0, 0, 0} : fit_ribbon(R, rows[t], d, p.delta, p.w_max);
+    };
+    if (len < 65536) fit(0, len);
+    else parallel_rows(len, fit);
+    // GrowSegments (Algorithm 4) over the listed rows; an unlisted row has k = 0
     std::vector<BandSeg> S;
-    int64_t i = 0;
-    while (i < m) {
-      if (ext[i].k == 0) {
-        ++i;
+    int64_t t = 0;
+    while (t < len) {
+      if (ext[t].k == 0) {
+        ++t;
         continue;
       }
-      const int64_t i0 = i;
-      int64_t L = ext[i].l, U = ext[i].u;
+      const int64_t i0 = rows[t];
+      int64_t L = ext[t].l, U = ext[t].u;
       int64_t z = ribbon_count(R, i0, d - L, d + U);
-      int64_t j = i + 1;
-      while (j < m && ext[j].k > 0) {
-        const int64_t L2 = std::max<int64_t>(L, ext[j].l), U2 = std::max<int64_t>(U, ext[j].u);
+      int64_t j = i0 + 1, u = t + 1;
+      while (u < len && rows[u] == j && ext[u].k > 0) {
+        const int64_t L2 = std::max<int64_t>(L, ext[u].l), U2 = std::max<int64_t>(U, ext[u].u);
         int64_t z2;
         if (L2 != L || U2 != U) {
           z2 = 0;
@@ -149,20 +167,21 @@ std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p) 
         U = U2;
         z = z2;
         ++j;
+        ++u;
       }
       if (j - i0 >= p.l_seg) S.push_back({i0, j, d, L, U, z});
-      i = j;
+      t = u;   // the next segment may start at row j (listed) or at the next listed row
     }
     if (S.empty()) continue;
     int64_t area = 0, zz = 0;
-    for (auto &s : S) {
-      area += (s.L + s.U + 1) * (s.i1 - s.i0);
-      zz += s.z;
+    for (auto &sg : S) {
+      area += (sg.L + sg.U + 1) * (sg.i1 - sg.i0);
+      zz += sg.z;
     }
     if (area < p.a_min || (double)zz / (double)area < p.delta) continue;
-    for (auto &s : S) {
-      for (int64_t r = s.i0; r < s.i1; ++r) used[r] = 1;
-      out.push_back(s);
+    for (auto &sg : S) {
+      for (int64_t r = sg.i0; r < sg.i1; ++r) used[r] = 1;
+      out.push_back(sg);
     }
   }
   return out;

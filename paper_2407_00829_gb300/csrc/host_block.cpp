@@ -66,18 +66,36 @@ void scan_start(const Csr &M, int64_t o0, int64_t O1, int64_t I0, int64_t I1,
                 const sable_extract_params &p, int64_t s_min, std::vector<int32_t> &H,
                 std::vector<int32_t> &touched, Best &best) {
   const int64_t L_in = I1 - I0;
-  int64_t tmin = INT64_MAX, tmax = -1;
+  int64_t tmin = INT64_MAX, tmax = -1, hmax = 0, total = 0;
+  const double ub_unit = std::pow(1.0 - p.delta, (double)kScoreExp);
   const int64_t o_end = std::min<int64_t>(O1, o0 + (int64_t)p.max_span);
   for (int64_t o1 = o0; o1 < o_end; ++o1) {
     const int32_t *b = M.ci.data() + M.rp[o1], *e = M.ci.data() + M.rp[o1 + 1];
     for (const int32_t *q = std::lower_bound(b, e, (int32_t)I0); q < e && *q < I1; ++q) {
       const int64_t rel = *q - I0;
-      if (H[rel]++ == 0) touched.push_back((int32_t)rel);
+      const int32_t h = ++H[rel];
+      if (h == 1) touched.push_back((int32_t)rel);
+      if (h > hmax) hmax = h;
+      ++total;
       if (rel < tmin) tmin = rel;
       if (rel > tmax) tmax = rel;
     }
     const int64_t s = o1 - o0 + 1;
     if (s < s_min || tmax < 0) continue;
+    // Exact shortcuts (the printed scan would record nothing for this span):
+    //  - every window's density is at most hmax / s;
+    //  - every window's score is at most ub(total) (see below), so it cannot
+    //    exceed the best score found so far, which only a strictly larger
+    //    score replaces.
+    if ((double)hmax < p.delta * (double)s) continue;
+    {
+      double ub;
+      if (total >= p.a_min) ub = (double)total * ub_unit;
+      else if ((double)total >= p.delta * (double)p.a_min)
+        ub = (double)p.a_min * std::pow((double)total / (double)p.a_min - p.delta, (double)kScoreExp);
+      else continue;
+      if (best.sc >= 0 && ub * (1.0 + 1e-9) <= best.sc) continue;
+    }
     // state of the printed scan after the leading empty slots [0, tmin)
     const int64_t w_small = (p.a_min + s - 1) / s - 1;   // widest window with area < a_min
     int64_t i0 = tmin - std::min<int64_t>(tmin, w_small);

@@ -39,7 +39,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="sable", choices=["sable", "reference"])
-    ap.add_argument("--workload", default="spmv1m", choices=["spmv1m", "spmv4096"])
+    ap.add_argument("--workload", default="spmv1m", choices=["spmv1m", "spmv4096", "batch512"])
+    ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmm", action="store_true")
     return ap.parse_args()
@@ -242,10 +243,94 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
     return out
 
 
+def run_batch(args):
+    """Many matrices of uneven size in one grouped launch per op: 512 seeded
+    matrices, rows log-uniform in [1k, 64k], 5-200 entries per row, mixed
+    band / block / scatter structure; VDIA+VBR+CSR plans; SpMV and SpMM with
+    N = 32 (FP32 and BF16 blocks), direct and replayed from a CUDA graph,
+    against one launch per matrix.  The whole batch (GBs of arrays) exceeds
+    L2 between launches."""
+    import concurrent.futures as cf
+    import torch
+    from paper_2407_00829_gb300 import build as sbuild
+    sbuild.build()
+    import paper_2407_00829_gb300 as sable
+    import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    mats = synth.batch_512(count=args.batch_count)
+    t_gen = time.perf_counter() - t0
+    plan_spec = [(sable.VDIA, None), (sable.VBR, dict(a_min=256)), (sable.CSR, None)]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        plans = list(ex.map(lambda A: sable.plan_from(A, plan_spec, upload=False), mats))
+    t_ex = time.perf_counter() - t0
+    for P in plans:
+        P.upload()
+    infos = [P.info() for P in plans]
+    B = sable.Batch(plans)
+    stream = torch.cuda.current_stream(dev)
+    xs = [torch.from_numpy(synth.dense_operand(i, A["n"])).to(dev) for i, A in enumerate(mats)]
+    ys = [torch.empty(A["m"], device=dev) for A in mats]
+    N = 32
+    Bs = [torch.from_numpy(synth.dense_operand(1000 + i, A["n"], N)).to(dev) for i, A in enumerate(mats)]
+    Cs = [torch.empty(A["m"], N, device=dev) for A in mats]
+    nnz = sum(i["nnz"] for i in infos)
+    vbytes = sum(i["spmv_bytes"] for i in infos)
+
+    def timed(fn, k):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / k
+
+    k = max(3, min(args.steps, 50))
+    gv = B.graph_spmv(xs, ys)
+    res = {"spmv_grouped_ms": timed(lambda: B.spmv(xs, ys, stream), k),
+           "spmv_graph_ms": timed(lambda: gv.launch(stream), k),
+           "spmv_per_matrix_ms": timed(lambda: [P.spmv(x, y, stream) for P, x, y in zip(plans, xs, ys)], 3)}
+    for prec, name in ((sable.FP32, "fp32"), (sable.BF16_BLOCKS, "bf16_blocks")):
+        g = B.graph_spmm(Bs, Cs, N, prec)
+        res[f"spmm_{name}_grouped_ms"] = timed(lambda: B.spmm(Bs, Cs, N, prec, stream), k)
+        res[f"spmm_{name}_graph_ms"] = timed(lambda: g.launch(stream), k)
+        g.close()
+    res["spmm_fp32_per_matrix_ms"] = timed(
+        lambda: [P.spmm(b, c, sable.FP32, stream) for P, b, c in zip(plans, Bs, Cs)], 3)
+    assert B.device_error() == 0
+    ms = res["spmv_graph_ms"]
+    line = {"metric": METRIC, "value": vbytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": k,
+            "warmup": 3, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch-{len(mats)}: rows log-uniform [1k, 64k], 5-200 entries/row, mixed "
+                                   "band/block/scatter, VDIA+VBR+CSR, one grouped launch per op (CUDA graph)",
+                       "matrices": len(mats), "nnz": nnz, "rows": sum(i["m"] for i in infos),
+                       "nnz_vdia": sum(i["nnz_vdia"] for i in infos), "nnz_vbr": sum(i["nnz_vbr"] for i in infos),
+                       "gen_s": round(t_gen, 1), "extract_s": round(t_ex, 1), "spmm_N": N},
+            "spmv_GB/s": vbytes / (ms * 1e-3) / 1e9,
+            "spmm_fp32_GFLOP/s": 2.0 * nnz * N / (res["spmm_fp32_graph_ms"] * 1e-3) / 1e9,
+            "spmm_bf16_GFLOP/s": 2.0 * nnz * N / (res["spmm_bf16_blocks_graph_ms"] * 1e-3) / 1e9,
+            "times_ms": res, "gpu_launches": 1}
+    print(json.dumps(line), flush=True)
+    gv.close()
+    B.close()
+    for P in plans:
+        P.close()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch512":
+        run_batch(args)
         return
     ws, rank, local = _dist()
     import torch

@@ -205,6 +205,47 @@ sable_status sable_graph_destroy(sable_graph_t graph);
 sable_status sable_batch_status(sable_batch_t batch, int32_t *device_error);
 sable_status sable_batch_destroy(sable_batch_t batch);
 
+/* ---- Learned planner support (the planner itself is a layer on top of the
+ * paper's pipeline; its knobs are the extractor order and thresholds of
+ * Section 3.2 / 4.1 / 4.2 and Section 5's delta) ----------------------------
+ *
+ * Structural features of a COO matrix (device arrays row/col, nnz entries):
+ * writes SABLE_NFEAT floats to `out` (device): sizes, row-length statistics
+ * and histogram, the share of entries on sparse / dense diagonals (the
+ * histogram M[d] of Algorithm 3), the share near the main diagonal, and the
+ * share of entries in dense 8 x 8 tiles (the block extractor's candidate test,
+ * counted in a hash table over at most 2^22 sampled entries).  The exact
+ * definitions are in the implementation's header comment.  `work` is a device
+ * workspace of at least sable_features_workspace_bytes(m, n, nnz) bytes.
+ * Errors: SABLE_ERR_INVALID; SABLE_ERR_CUDA. */
+#define SABLE_NFEAT 24
+int64_t sable_features_workspace_bytes(int64_t m, int64_t n, int64_t nnz);
+sable_status sable_features(int64_t m, int64_t n, int64_t nnz, const int32_t *row, const int32_t *col,
+                            void *work, int64_t work_bytes, float *out, void *stream);
+
+/* A multilayer perceptron n_in -> n_h1 (ReLU) -> n_h2 (ReLU) -> n_out (linear),
+ * FP32.  Parameters live in one caller-owned device buffer of
+ * sable_mlp_param_count() floats: W1 [n_in x n_h1], b1, W2 [n_h1 x n_h2], b2,
+ * W3 [n_h2 x n_out], b3, matrices row-major.  `work` is a device workspace of
+ * sable_mlp_work_floats(shape, batch) floats.  X is [batch x n_in], Y and T
+ * are [batch x n_out], row-major, device. */
+typedef struct {
+  int32_t n_in, n_h1, n_h2, n_out;
+} sable_mlp_shape;
+int64_t sable_mlp_param_count(const sable_mlp_shape *shape);
+int64_t sable_mlp_work_floats(const sable_mlp_shape *shape, int64_t batch);
+/* Y = MLP(X). */
+sable_status sable_mlp_forward(const sable_mlp_shape *shape, const float *params, const float *X, int64_t batch,
+                               float *Y, float *work, void *stream);
+/* Forward, masked mean squared error L = sum mask (Y - T)^2 / sum mask (mask
+ * NULL = all ones; written to *loss, device, if loss is not NULL) and the
+ * gradient dL/dparams into `grads` (same layout as params). */
+sable_status sable_mlp_grad(const sable_mlp_shape *shape, const float *params, const float *X, const float *T,
+                            const float *mask, int64_t batch, float *grads, float *loss, float *work, void *stream);
+/* One Adam step (bias-corrected, step >= 1) on `count` parameters. */
+sable_status sable_mlp_adam(int64_t count, float *params, const float *grads, float *m, float *v, int64_t step,
+                            float lr, float beta1, float beta2, float eps, void *stream);
+
 /* Calibration: `count` random 4-byte reads of x[0..n) (device), indices from a
  * fixed hash reduced modulo n, one kernel launch on `stream`; `out` (device,
  * one float) may be written.  Timing it gives the device's rate of random

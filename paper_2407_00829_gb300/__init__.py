@@ -31,8 +31,16 @@ EXPORTED = [
     "sable_plan_set_tiling", "sable_plan_status", "sable_plan_destroy", "sable_status_string",
     "sable_probe_gather", "sable_batch_create", "sable_batch_spmv", "sable_batch_spmm",
     "sable_batch_graph_spmv", "sable_batch_graph_spmm", "sable_graph_launch", "sable_graph_destroy",
-    "sable_batch_status", "sable_batch_destroy",
+    "sable_batch_status", "sable_batch_destroy", "sable_features_workspace_bytes", "sable_features",
+    "sable_mlp_param_count", "sable_mlp_work_floats", "sable_mlp_forward", "sable_mlp_grad", "sable_mlp_adam",
 ]
+
+NFEAT = 24
+
+
+class MlpShape(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("n_h1", ctypes.c_int32), ("n_h2", ctypes.c_int32),
+                ("n_out", ctypes.c_int32)]
 
 
 class SableError(RuntimeError):
@@ -96,6 +104,14 @@ def lib():
             "sable_graph_destroy": ([p], i32),
             "sable_batch_status": ([p, p], i32),
             "sable_batch_destroy": ([p], i32),
+            "sable_features_workspace_bytes": ([i64, i64, i64], i64),
+            "sable_features": ([i64, i64, i64, p, p, p, i64, p, p], i32),
+            "sable_mlp_param_count": ([p], i64),
+            "sable_mlp_work_floats": ([p, i64], i64),
+            "sable_mlp_forward": ([p, p, p, i64, p, p, p], i32),
+            "sable_mlp_grad": ([p, p, p, p, p, i64, p, p, p, p], i32),
+            "sable_mlp_adam": ([i64, p, p, p, p, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, p], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -337,6 +353,71 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def features(m, n, row, col, stream=None):
+    """SABLE_NFEAT structural features of a COO matrix given as device int32
+    tensors (computed by the library's feature kernels); returns a device tensor."""
+    import torch
+    nnz = row.numel()
+    wb = lib().sable_features_workspace_bytes(int(m), int(n), int(nnz))
+    work = torch.empty(max(wb, 16), dtype=torch.uint8, device=row.device)
+    out = torch.empty(NFEAT, dtype=torch.float32, device=row.device)
+    _check(lib().sable_features(int(m), int(n), int(nnz), _dptr(row), _dptr(col), _dptr(work), wb, _dptr(out),
+                                _stream_handle(stream)), "sable_features")
+    return out
+
+
+class Mlp:
+    """Device MLP n_in -> h1 -> h2 -> n_out (ReLU, ReLU, linear) trained with the
+    library's kernels; parameters / Adam state are torch device tensors."""
+
+    def __init__(self, n_in, h1, h2, n_out, seed=0, device="cuda"):
+        import torch
+        self.shape = MlpShape(n_in, h1, h2, n_out)
+        self.count = lib().sable_mlp_param_count(ctypes.byref(self.shape))
+        rng = np.random.default_rng(seed)
+        parts = []
+        for a, b in ((n_in, h1), (h1, h2), (h2, n_out)):
+            parts.append(rng.standard_normal((a, b)) * np.sqrt(2.0 / a))
+            parts.append(np.zeros(b))
+        flat = np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+        assert flat.size == self.count
+        self.params = torch.from_numpy(flat).to(device)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+        self._work = {}
+
+    def _w(self, batch):
+        import torch
+        if batch not in self._work:
+            n = lib().sable_mlp_work_floats(ctypes.byref(self.shape), int(batch))
+            self._work[batch] = torch.empty(n, dtype=torch.float32, device=self.params.device)
+        return self._work[batch]
+
+    def forward(self, X, stream=None):
+        import torch
+        B = X.shape[0]
+        Y = torch.empty(B, self.shape.n_out, dtype=torch.float32, device=X.device)
+        _check(lib().sable_mlp_forward(ctypes.byref(self.shape), _dptr(self.params), _dptr(X), B, _dptr(Y),
+                                       _dptr(self._w(B)), _stream_handle(stream)), "sable_mlp_forward")
+        return Y
+
+    def grad(self, X, T, mask=None, stream=None):
+        import torch
+        B = X.shape[0]
+        loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+        _check(lib().sable_mlp_grad(ctypes.byref(self.shape), _dptr(self.params), _dptr(X), _dptr(T),
+                                    _dptr(mask) if mask is not None else None, B, _dptr(self.grads),
+                                    _dptr(loss), _dptr(self._w(B)), _stream_handle(stream)), "sable_mlp_grad")
+        return loss
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self.step += 1
+        _check(lib().sable_mlp_adam(self.count, _dptr(self.params), _dptr(self.grads), _dptr(self.m), _dptr(self.v),
+                                    self.step, lr, beta1, beta2, eps, _stream_handle(stream)), "sable_mlp_adam")
 
 
 def plan_from(A: dict, extractors, tiling: Optional[dict] = None, upload: bool = True, stream=None) -> Plan:

@@ -223,6 +223,34 @@ int64_t sable_features_workspace_bytes(int64_t m, int64_t n, int64_t nnz);
 sable_status sable_features(int64_t m, int64_t n, int64_t nnz, const int32_t *row, const int32_t *col,
                             void *work, int64_t work_bytes, float *out, void *stream);
 
+/* sable_features without a caller workspace and without any allocation.  The
+ * paper has no counterpart: this entry point serves callers that may not call
+ * cudaMalloc, for instance a host framework that owns all of a GPU's memory
+ * through its own pool and forbids outside allocations, a plugin interface
+ * that hands over only input and output pointers, or latency-critical code
+ * that cannot take the device-wide synchronisation cudaMalloc / cudaFree may
+ * cause.  The scratch (row and diagonal counters, the tile hash table) is one
+ * fixed array of SABLE_FEATURES_NOALLOC_MAX_BYTES (32 MiB) that every GPU
+ * holds from loading the library's device code until the process exits.
+ *  - Same inputs, output and results as sable_features; no workspace argument.
+ *  - Sizes whose workspace, sable_features_workspace_bytes(m, n, nnz), exceeds
+ *    SABLE_FEATURES_NOALLOC_MAX_BYTES are rejected with SABLE_ERR_UNSUPPORTED
+ *    before any device work (for example nnz <= 2^20 with 2m + n <= 2,000,000 fits).
+ *  - The first call on a device looks up that device's address of the array
+ *    (cudaGetSymbolAddress, with the device current); make that first call
+ *    before any stream capture.
+ *  - The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ *    routine.  It clears the array's counters and table on `stream` before
+ *    using them, since the array keeps the previous call's contents.
+ *  - All calls on a device share the one array: calls that may overlap on the
+ *    GPU (other streams, other host threads) race and give wrong features;
+ *    order them (one stream, or events).
+ * Errors: SABLE_ERR_INVALID (bad arguments); SABLE_ERR_UNSUPPORTED (too
+ * large, or device ordinal >= 64); SABLE_ERR_CUDA. */
+#define SABLE_FEATURES_NOALLOC_MAX_BYTES (32 << 20)
+sable_status sable_features_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row, const int32_t *col,
+                                    float *out, void *stream);
+
 /* A multilayer perceptron n_in -> n_h1 (ReLU) -> n_h2 (ReLU) -> n_out (linear),
  * FP32.  Parameters live in one caller-owned device buffer of
  * sable_mlp_param_count() floats: W1 [n_in x n_h1], b1, W2 [n_h1 x n_h2], b2,

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "sable_internal.h"
 
@@ -304,6 +305,33 @@ void forward(const sable_mlp_shape &s, const float *P, const float *X, int64_t B
 
 using namespace sable;
 
+// Scratch of sable_features_noalloc: one fixed device array, created when the
+// library's device code is loaded on a GPU and held there until the process
+// exits.  Host code may not use the symbol's host-side address; each device's
+// own address is looked up once (with that device current) and then passed to
+// the kernels.
+static __device__ __align__(256) unsigned char g_feat_scratch[SABLE_FEATURES_NOALLOC_MAX_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+sable_status feat_scratch_address(void **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SABLE_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return SABLE_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_feat_scratch) != cudaSuccess || !p) return SABLE_ERR_CUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return SABLE_OK;
+}
+}  // namespace
+
 extern "C" {
 
 int64_t sable_features_workspace_bytes(int64_t m, int64_t n, int64_t nnz) {
@@ -325,6 +353,40 @@ sable_status sable_features(int64_t m, int64_t n, int64_t nnz, const int32_t *ro
   unsigned long long *acc = reinterpret_cast<unsigned long long *>(base + w.o_acc);
   cudaError_t e = cudaMemsetAsync(base, 0, w.o_keys, st);                       // rowlen, dcount
   if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0xff, (size_t)w.slots * 8, st);  // empty keys
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)w.slots * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 32 * 8, st);
+  if (e != cudaSuccess) return SABLE_ERR_CUDA;
+  const int64_t ntc = (n + 7) / 8;
+  const int grid = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (nnz + kThreads - 1) / kThreads));
+  if (nnz > 0) {
+    feat_count<<<grid, kThreads, 0, st>>>(nnz, row, col, m, rowlen, dcount, keys, cnt, w.slots, w.stride, ntc, acc);
+    feat_tiles<<<grid, kThreads, 0, st>>>(nnz, row, col, keys, cnt, w.slots, w.stride, ntc, acc);
+  }
+  const int64_t nd = m + n > 0 ? m + n - 1 : 0;
+  const int gridr = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (std::max(m, nd) + kThreads - 1) / kThreads));
+  feat_reduce<<<gridr, kThreads, 0, st>>>(m, nd, rowlen, dcount, std::max<int64_t>(1, std::min(m, n)), acc);
+  feat_final<<<1, 32, 0, st>>>(m, n, nnz, acc, out);
+  return cudaGetLastError() == cudaSuccess ? SABLE_OK : SABLE_ERR_CUDA;
+}
+
+sable_status sable_features_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row, const int32_t *col,
+                                    float *out, void *stream) {
+  if (m < 0 || n < 0 || nnz < 0 || !out || (nnz > 0 && (!row || !col))) return SABLE_ERR_INVALID;
+  const FeatWork w = feat_layout(m, n, nnz);
+  if (w.total > (size_t)SABLE_FEATURES_NOALLOC_MAX_BYTES) return SABLE_ERR_UNSUPPORTED;
+  void *scratch = nullptr;
+  const sable_status got = feat_scratch_address(&scratch);
+  if (got != SABLE_OK) return got;
+  cudaStream_t st = (cudaStream_t)stream;
+  char *base = static_cast<char *>(scratch);
+  int32_t *rowlen = reinterpret_cast<int32_t *>(base + w.o_rowlen);
+  int32_t *dcount = reinterpret_cast<int32_t *>(base + w.o_dcount);
+  unsigned long long *keys = reinterpret_cast<unsigned long long *>(base + w.o_keys);
+  int32_t *cnt = reinterpret_cast<int32_t *>(base + w.o_cnt);
+  unsigned long long *acc = reinterpret_cast<unsigned long long *>(base + w.o_acc);
+  // the array keeps the previous call's contents: reset counters and the table
+  cudaError_t e = cudaMemsetAsync(base, 0, w.o_keys, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0xff, (size_t)w.slots * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)w.slots * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 32 * 8, st);
   if (e != cudaSuccess) return SABLE_ERR_CUDA;

@@ -113,6 +113,23 @@ sable_status sable_plan_create(int64_t m, int64_t n, int64_t nnz, const int32_t 
 sable_status sable_plan_add_extractor(sable_plan_t plan, sable_extractor kind,
                                       const sable_extract_params *params);
 
+/* Append a stage of given regions instead of a search: the saved region
+ * table of an earlier extraction, so that a plan can be rebuilt without
+ * running the extractors again, e.g. for the same structure with new values
+ * (the paper keeps its extracted regions on disk and reuses them when only
+ * the values change, Section 3.4).  kind SABLE_X_VDIA: `count` rows of
+ * (row_start, nrows, lowest offset j - i, ndiags), rows within [0, m),
+ * offsets within [-(m-1), n-1]; kind SABLE_X_VBR: `count` rows of (row0,
+ * nrows, col0, ncols) inside the matrix.  int64, row-major, copied.  At
+ * sable_extract the stage runs in its place among the stages: its regions,
+ * in the given order, claim the residual entries inside their areas that no
+ * earlier region claimed; a region is kept even if it claims nothing.  With
+ * sable_plan_get_region_stages this reproduces an extraction exactly.
+ * Errors: SABLE_ERR_ORDER after sable_extract; SABLE_ERR_INVALID (kind CSR,
+ * a region outside the matrix, count < 0); SABLE_ERR_OOM. */
+sable_status sable_plan_add_regions(sable_plan_t plan, sable_extractor kind, const int64_t *regions,
+                                    int64_t count);
+
 /* Run the extractors in order over the residual, check that the residual is
  * empty and that the regions partition the entries exactly, and build the
  * host tables (Section 3, "Extract"/"Dispatch", Section 3.4).  Host only: no
@@ -162,6 +179,18 @@ sable_status sable_plan_get_blocks(sable_plan_t plan, int64_t *out);
 sable_status sable_plan_get_vdia_values(sable_plan_t plan, float *out);
 sable_status sable_plan_get_vbr_values(sable_plan_t plan, float *out);
 sable_status sable_plan_get_csr(sable_plan_t plan, int64_t *row_ptr, int32_t *col, float *val);
+/* The stage (0-based position among the extractors and region stages, in the
+ * order they were added) that produced each segment and each block, in the
+ * order of sable_plan_get_segments / sable_plan_get_blocks: n_segments and
+ * n_blocks int32.  Together they are the plan's region table. */
+sable_status sable_plan_get_region_stages(sable_plan_t plan, int32_t *seg_stage, int32_t *blk_stage);
+
+/* Start the plan over from its canonical matrix: drop the stages, the
+ * extraction and the device tables (cudaFree, which waits for the device),
+ * keep the matrix and the tiling, clear the recorded error.  New stages can
+ * then be added and extracted: one matrix, many plans, without copying and
+ * sorting the COO input again.  Errors: SABLE_ERR_INVALID; SABLE_ERR_CUDA. */
+sable_status sable_plan_reset(sable_plan_t plan);
 
 /* Tuning of the row tiles one launch works on; takes effect at the next
  * upload.  spmv_rows: rows of an SpMV tile, a multiple of 4 in [4, 1024];

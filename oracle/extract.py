@@ -40,7 +40,14 @@ same readings, written independently):
   area; 8-connected hot cells form components whose bounding boxes, grown
   by one cell on each side and clipped, are merged until disjoint, sorted by
   (row, column), and Decompose runs on each box instead of on the whole
-  matrix.  ``tile`` = 0 runs Algorithm 1 on the whole matrix.
+  matrix.  ``tile`` = 0 runs Algorithm 1 on the whole matrix.  A component
+  spanning more than S = ceil(max_span / tile) cell rows whose cells fill
+  under a quarter of its bounding box (a diagonal band) gives instead one box
+  per slab of S cell rows counted from its first row: its cells' bounding box
+  in that slab, grown by one cell in columns and, at the component's first and
+  last slab, outward in rows.  Without the cut, a long band makes one box as
+  large as the matrix and Algorithm 1's recursion along it costs
+  O(rows^2 x entries per row).
 """
 from __future__ import annotations
 
@@ -301,14 +308,17 @@ def candidate_regions(R: Residual, p: Params):
             hot.add((I, J))
     seen = set()
     boxes = []
+    S = max(1, -(-p.max_span // g))            # slab height in cells
     for t in sorted(hot):
         if t in seen:
             continue
         stack = [t]
         seen.add(t)
+        comp = []
         I0, I1, J0, J1 = t[0], t[0] + 1, t[1], t[1] + 1
         while stack:
             a, b = stack.pop()
+            comp.append((a, b))
             I0, I1, J0, J1 = min(I0, a), max(I1, a + 1), min(J0, b), max(J1, b + 1)
             for da in (-1, 0, 1):
                 for db in (-1, 0, 1):
@@ -316,7 +326,15 @@ def candidate_regions(R: Residual, p: Params):
                     if q in hot and q not in seen:
                         seen.add(q)
                         stack.append(q)
-        boxes.append([max(0, I0 - 1), min(TI, I1 + 1), max(0, J0 - 1), min(TJ, J1 + 1)])
+        if I1 - I0 > S and 4 * len(comp) < (I1 - I0) * (J1 - J0):
+            # a tall component filling under a quarter of its box: one box per slab
+            for a in range(I0, I1, S):
+                b = min(I1, a + S)
+                cols = [c for (r, c) in comp if a <= r < b]
+                boxes.append([max(0, a - 1) if a == I0 else a, min(TI, b + 1) if b == I1 else b,
+                              max(0, min(cols) - 1), min(TJ, max(cols) + 2)])
+        else:
+            boxes.append([max(0, I0 - 1), min(TI, I1 + 1), max(0, J0 - 1), min(TJ, J1 + 1)])
     merged = True
     while merged:
         merged = False

@@ -33,6 +33,7 @@ EXPORTED = [
     "sable_batch_graph_spmv", "sable_batch_graph_spmm", "sable_graph_launch", "sable_graph_destroy",
     "sable_batch_status", "sable_batch_destroy", "sable_features_workspace_bytes", "sable_features",
     "sable_mlp_param_count", "sable_mlp_work_floats", "sable_mlp_forward", "sable_mlp_grad", "sable_mlp_adam",
+    "sable_plan_add_regions", "sable_plan_get_region_stages", "sable_plan_reset",
 ]
 
 NFEAT = 24
@@ -106,6 +107,9 @@ def lib():
             "sable_batch_destroy": ([p], i32),
             "sable_features_workspace_bytes": ([i64, i64, i64], i64),
             "sable_features": ([i64, i64, i64, p, p, p, i64, p, p], i32),
+            "sable_plan_add_regions": ([p, i32, p, i64], i32),
+            "sable_plan_get_region_stages": ([p, p, p], i32),
+            "sable_plan_reset": ([p], i32),
             "sable_mlp_param_count": ([p], i64),
             "sable_mlp_work_floats": ([p, i64], i64),
             "sable_mlp_forward": ([p, p, p, i64, p, p, p], i32),
@@ -161,6 +165,7 @@ class Plan:
                "sable_plan_create")
         self._h = h
         self.m, self.n = int(m), int(n)
+        self._stages = []
 
     # -- life cycle
     def close(self):
@@ -189,6 +194,52 @@ class Plan:
         for k, v in kw.items():
             setattr(p, k, v)
         _check(lib().sable_plan_add_extractor(self._h, kind, ctypes.byref(p)), "add_extractor")
+        self._stages.append(kind)
+        return self
+
+    def add_regions(self, kind: int, regions):
+        """A stage of given regions (k x 4 int64: VDIA (row0, nrows, off_lo,
+        ndiag) or VBR (row0, nrows, col0, ncols)) in place of a search."""
+        g = np.ascontiguousarray(np.asarray(regions, dtype=np.int64).reshape(-1, 4))
+        _check(lib().sable_plan_add_regions(self._h, kind, g.ctypes.data, g.shape[0]), "add_regions")
+        self._stages.append(kind)
+        return self
+
+    def reset(self):
+        """Drop stages, extraction and device tables; keep the matrix."""
+        _check(lib().sable_plan_reset(self._h), "sable_plan_reset")
+        self._stages = []
+        return self
+
+    def region_stages(self):
+        info = self.info()
+        ss = np.zeros(max(1, info["n_segments"]), dtype=np.int32)
+        bs = np.zeros(max(1, info["n_blocks"]), dtype=np.int32)
+        _check(lib().sable_plan_get_region_stages(self._h, ss.ctypes.data, bs.ctypes.data), "get_region_stages")
+        return ss[:info["n_segments"]], bs[:info["n_blocks"]]
+
+    def region_table(self):
+        """The extracted plan as stages [(kind, regions k x 4)]: VDIA / VBR
+        stages carry their regions, CSR stages none.  ``add_stages`` on a plan
+        of the same matrix rebuilds this extraction without searching."""
+        ss, bs = self.region_stages()
+        segs, blks = self.segments(), self.blocks()
+        out = []
+        for t, kind in enumerate(self._stages):
+            if kind == VDIA:
+                out.append((kind, segs[ss == t]))
+            elif kind == VBR:
+                out.append((kind, blks[bs == t]))
+            else:
+                out.append((kind, np.zeros((0, 4), np.int64)))
+        return out
+
+    def add_stages(self, table):
+        for kind, regions in table:
+            if kind == CSR:
+                self.add_extractor(CSR)
+            else:
+                self.add_regions(kind, regions)
         return self
 
     def extract(self):
@@ -263,6 +314,20 @@ class Plan:
 
     def status(self) -> int:
         return lib().sable_plan_status(self._h)
+
+
+def save_region_table(path, table, m: int, n: int, nnz: int):
+    """Write a region table (``Plan.region_table()``) to an .npz file."""
+    arrs = {f"stage{t}": np.asarray(g, np.int64) for t, (_, g) in enumerate(table)}
+    np.savez(path, kinds=np.array([k for k, _ in table], np.int32), shape=np.array([m, n, nnz], np.int64),
+             **arrs)
+
+
+def load_region_table(path):
+    """Read a region table: ([(kind, regions)], (m, n, nnz))."""
+    d = np.load(path)
+    kinds = d["kinds"].tolist()
+    return [(k, d[f"stage{t}"]) for t, k in enumerate(kinds)], tuple(int(v) for v in d["shape"])
 
 
 def probe_gather(x, count: int, out, stream=None):

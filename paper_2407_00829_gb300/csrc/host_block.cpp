@@ -17,7 +17,12 @@
 //    matrix: cells of tile x tile with entries >= delta * cell area are hot,
 //    8-connected hot cells form components, their bounding boxes (grown by one
 //    cell, clipped) are merged until disjoint and visited in (row, column)
-//    order.
+//    order.  A component taller than max_span rows whose hot cells fill less
+//    than a quarter of its bounding box (a diagonal band) gives instead one
+//    box per slab of ceil(max_span / tile) cell rows, counted from its first
+//    row: the bounding box of its cells in that slab, grown by one cell in
+//    columns and, at the component's two ends, in rows.  Slabs touch but do
+//    not overlap, so the merge keeps them apart.
 //  The two scan shortcuts below (starting a window scan at the first
 //  non-empty histogram slot, stopping once the window is past the last one)
 //  reproduce the printed loop's results exactly, given delta > 0.
@@ -223,15 +228,18 @@ std::vector<Region> candidate_regions(const Csr &R, const sable_extract_params &
   keys.shrink_to_fit();
   std::vector<uint8_t> seen(hot.size(), 0);
   std::vector<std::array<int64_t, 4>> boxes;
-  std::vector<size_t> stack;
+  std::vector<size_t> stack, comp;
+  const int64_t S = std::max<int64_t>(1, ((int64_t)p.max_span + g - 1) / g);   // slab height, tiles
   for (size_t t = 0; t < hot.size(); ++t) {
     if (seen[t]) continue;
     seen[t] = 1;
     stack.assign(1, t);
+    comp.clear();
     int64_t I0 = hot[t] / TJ, I1 = I0 + 1, J0 = hot[t] % TJ, J1 = J0 + 1;
     while (!stack.empty()) {
       const size_t q = stack.back();
       stack.pop_back();
+      comp.push_back(q);
       const int64_t a = hot[q] / TJ, b = hot[q] % TJ;
       I0 = std::min(I0, a);
       I1 = std::max(I1, a + 1);
@@ -251,8 +259,25 @@ std::vector<Region> candidate_regions(const Csr &R, const sable_extract_params &
           }
         }
     }
-    boxes.push_back({std::max<int64_t>(0, I0 - 1), std::min(TI, I1 + 1), std::max<int64_t>(0, J0 - 1),
-                     std::min(TJ, J1 + 1)});
+    if (I1 - I0 > S && (int64_t)comp.size() * 4 < (I1 - I0) * (J1 - J0)) {
+      // tall, sparsely filled component (a band): one box per slab of S tile rows
+      for (int64_t a = I0; a < I1; a += S) {
+        const int64_t b = std::min(I1, a + S);
+        int64_t s0 = INT64_MAX, s1 = -1;
+        for (size_t q : comp) {
+          const int64_t r = hot[q] / TJ, c = hot[q] % TJ;
+          if (r >= a && r < b) {
+            s0 = std::min(s0, c);
+            s1 = std::max(s1, c + 1);
+          }
+        }
+        boxes.push_back({a == I0 ? std::max<int64_t>(0, a - 1) : a, b == I1 ? std::min(TI, b + 1) : b,
+                         std::max<int64_t>(0, s0 - 1), std::min(TJ, s1 + 1)});
+      }
+    } else {
+      boxes.push_back({std::max<int64_t>(0, I0 - 1), std::min(TI, I1 + 1), std::max<int64_t>(0, J0 - 1),
+                       std::min(TJ, J1 + 1)});
+    }
   }
   bool merged = true;
   while (merged) {

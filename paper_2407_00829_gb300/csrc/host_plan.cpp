@@ -141,6 +141,39 @@ sable_status sable_plan_add_extractor(sable_plan_t P, sable_extractor kind,
       p.tile < 0)
     return SABLE_ERR_INVALID;
   P->extractors.push_back({kind, p});
+  P->stage_regions.emplace_back();
+  P->stage_fixed.push_back(0);
+  return SABLE_OK;
+}
+
+sable_status sable_plan_add_regions(sable_plan_t P, sable_extractor kind, const int64_t *regions,
+                                    int64_t count) {
+  if (!P) return SABLE_ERR_INVALID;
+  if (P->sticky) return P->sticky;
+  if (P->extracted) return SABLE_ERR_ORDER;
+  if ((kind != SABLE_X_VDIA && kind != SABLE_X_VBR) || count < 0 || (count > 0 && !regions))
+    return SABLE_ERR_INVALID;
+  for (int64_t t = 0; t < count; ++t) {
+    const int64_t *g = regions + 4 * t;
+    if (kind == SABLE_X_VDIA) {
+      // rows [row0, row0 + nrows), offsets off_lo .. off_lo + ndiag - 1 within [-(m-1), n-1]
+      if (g[0] < 0 || g[1] < 1 || g[1] > P->m - g[0] || g[3] < 1 || g[2] < -(P->m - 1) ||
+          g[3] > P->n - g[2] || g[3] > INT32_MAX / 4)
+        return SABLE_ERR_INVALID;
+    } else {
+      if (g[0] < 0 || g[1] < 1 || g[1] > P->m - g[0] || g[2] < 0 || g[3] < 1 || g[3] > P->n - g[2])
+        return SABLE_ERR_INVALID;
+    }
+  }
+  try {
+    sable_extract_params p;
+    sable_default_params(kind, &p);
+    P->extractors.push_back({kind, p});
+    P->stage_regions.emplace_back(regions, regions + 4 * count);
+    P->stage_fixed.push_back(1);
+  } catch (const std::bad_alloc &) {
+    return fail(P, SABLE_ERR_OOM);
+  }
   return SABLE_OK;
 }
 
@@ -154,15 +187,46 @@ sable_status sable_extract(sable_plan_t P) {
     std::vector<int32_t> region(nnz, -1);
     std::vector<Segment> segs;   // acceptance order
     std::vector<Block> blks;
-    for (auto &ex : P->extractors) {
+    std::vector<int32_t> sstage, bstage;
+    for (size_t st = 0; st < P->extractors.size(); ++st) {
+      const auto &ex = P->extractors[st];
       const sable_extract_params &p = ex.second;
       Csr R = residual(*P, false);
-      if (ex.first == SABLE_X_CSR) {
+      if (P->stage_fixed[st]) {
+        // given regions, in order: each claims the stage's residual entries in
+        // its area that no earlier region of the stage claimed
+        const std::vector<int64_t> &G = P->stage_regions[st];
+        for (size_t t = 0; t + 3 < G.size(); t += 4) {
+          const int64_t r0 = G[t], nr = G[t + 1];
+          const int64_t lo = G[t + 2], hi = G[t + 2] + G[t + 3] - 1;   // offsets (VDIA) or columns (VBR)
+          const bool vd = ex.first == SABLE_X_VDIA;
+          const int32_t rid = (int32_t)(vd ? segs.size() : blks.size());
+          if (vd) {
+            segs.push_back({r0, nr, G[t + 2], G[t + 3]});
+            sstage.push_back((int32_t)st);
+          } else {
+            blks.push_back({r0, nr, G[t + 2], G[t + 3]});
+            bstage.push_back((int32_t)st);
+          }
+          for (int64_t r = r0; r < r0 + nr; ++r) {
+            const int64_t clo = vd ? r + lo : lo, chi = vd ? r + hi : hi;
+            const int32_t *b = R.ci.data() + R.rp[r], *e = R.ci.data() + R.rp[r + 1];
+            for (const int32_t *q = std::lower_bound(b, e, (int32_t)std::max<int64_t>(clo, 0));
+                 q < e && *q <= chi; ++q) {
+              const int64_t k = R.id[q - R.ci.data()];
+              if (P->owner[k] >= 0) continue;
+              P->owner[k] = vd ? OWN_VDIA : OWN_VBR;
+              region[k] = rid;
+            }
+          }
+        }
+      } else if (ex.first == SABLE_X_CSR) {
         for (int64_t q = 0; q < R.nnz(); ++q) P->owner[R.id[q]] = OWN_CSR;
       } else if (ex.first == SABLE_X_VDIA) {
         for (const BandSeg &s : extract_bands(R, p)) {
           const int32_t sid = (int32_t)segs.size();
           segs.push_back({s.i0, s.i1 - s.i0, s.d - s.L, s.L + s.U + 1});
+          sstage.push_back((int32_t)st);
           for (int64_t r = s.i0; r < s.i1; ++r)
             for (int64_t q = R.rp[r]; q < R.rp[r + 1]; ++q) {
               const int64_t o = (int64_t)R.ci[q] - r;
@@ -177,6 +241,7 @@ sable_status sable_extract(sable_plan_t P) {
         for (const BlockFound &b : partition_blocks(R, RT, p)) {
           const int32_t bid = (int32_t)blks.size();
           blks.push_back({b.r0, b.r1 - b.r0, b.c0, b.c1 - b.c0});
+          bstage.push_back((int32_t)st);
           for (int64_t r = b.r0; r < b.r1; ++r)
             for (int64_t q = R.rp[r]; q < R.rp[r + 1]; ++q)
               if (R.ci[q] >= b.c0 && R.ci[q] < b.c1) {
@@ -205,14 +270,18 @@ sable_status sable_extract(sable_plan_t P) {
     std::vector<int32_t> sidx(segs.size()), bidx(blks.size());
     std::vector<int64_t> sptr(segs.size() + 1, 0), bptr(blks.size() + 1, 0);
     H.segs.clear();
+    P->seg_stage.assign(so.size(), 0);
+    P->blk_stage.assign(bo.size(), 0);
     for (size_t t = 0; t < so.size(); ++t) {
       sidx[so[t]] = (int32_t)t;
+      P->seg_stage[t] = sstage[so[t]];
       H.segs.push_back(segs[so[t]]);
       sptr[t + 1] = sptr[t] + segs[so[t]].nrows * segs[so[t]].ndiag;
     }
     H.blks.clear();
     for (size_t t = 0; t < bo.size(); ++t) {
       bidx[bo[t]] = (int32_t)t;
+      P->blk_stage[t] = bstage[bo[t]];
       H.blks.push_back(blks[bo[t]]);
       bptr[t + 1] = bptr[t] + blks[bo[t]].nr * blks[bo[t]].nc;
     }
@@ -298,6 +367,15 @@ sable_status sable_plan_get_blocks(sable_plan_t P, int64_t *out) {
     out[4 * b + 2] = g.c0;
     out[4 * b + 3] = g.nc;
   }
+  return SABLE_OK;
+}
+
+sable_status sable_plan_get_region_stages(sable_plan_t P, int32_t *seg_stage, int32_t *blk_stage) {
+  if (!P) return SABLE_ERR_INVALID;
+  if (!P->extracted) return SABLE_ERR_ORDER;
+  if ((!seg_stage && !P->seg_stage.empty()) || (!blk_stage && !P->blk_stage.empty())) return SABLE_ERR_INVALID;
+  if (!P->seg_stage.empty()) std::memcpy(seg_stage, P->seg_stage.data(), P->seg_stage.size() * 4);
+  if (!P->blk_stage.empty()) std::memcpy(blk_stage, P->blk_stage.data(), P->blk_stage.size() * 4);
   return SABLE_OK;
 }
 

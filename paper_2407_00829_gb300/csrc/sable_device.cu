@@ -629,6 +629,42 @@ sable_status sable_csr_spmm(sable_plan_t P, const float *B, int64_t N, int64_t l
   return launch_spmm(P, P->dev_plain, B, N, ldb, C, ldc, false, (cudaStream_t)stream);
 }
 
+sable_status sable_plan_reset(sable_plan_t P) {
+  if (!P) return SABLE_ERR_INVALID;
+  if (P->dev_blob) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != P->device) cudaSetDevice(P->device);
+    const cudaError_t e = cudaFree(P->dev_blob);
+    if (cur >= 0 && cur != P->device) cudaSetDevice(cur);
+    P->dev_blob = nullptr;
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(P, SABLE_ERR_CUDA);
+    }
+  }
+  P->dev_bytes = 0;
+  P->dev = DevHybrid{};
+  P->dev_plain = DevHybrid{};
+  P->dev_self = nullptr;
+  P->dev_trip = nullptr;
+  P->dev_err = nullptr;
+  P->h_items_v.clear();
+  P->h_items_m.clear();
+  P->h_trip.clear();
+  P->extractors.clear();
+  P->stage_regions.clear();
+  P->stage_fixed.clear();
+  P->seg_stage.clear();
+  P->blk_stage.clear();
+  P->owner.assign(P->canon.ci.size(), OWN_NONE);
+  P->hyb = Hybrid{};
+  P->stats = sable_plan_stats{};
+  P->extracted = P->uploaded = false;
+  P->sticky = SABLE_OK;
+  return SABLE_OK;
+}
+
 sable_status sable_plan_destroy(sable_plan_t P) {
   if (!P) return SABLE_OK;
   if (P->dev_blob) {

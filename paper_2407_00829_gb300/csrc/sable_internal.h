@@ -125,6 +125,9 @@ struct sable_plan_s {
   sable::Csr canon;                    // canonical matrix (sorted, duplicates summed)
   std::vector<float> cval;             // canonical values
   std::vector<std::pair<sable_extractor, sable_extract_params>> extractors;
+  std::vector<std::vector<int64_t>> stage_regions;   // per stage: given regions (4 values each)
+  std::vector<uint8_t> stage_fixed;                  // per stage: 1 = given regions, 0 = search
+  std::vector<int32_t> seg_stage, blk_stage;         // stage of each segment / block (sorted order)
   std::vector<int8_t> owner;           // per canonical entry
   sable::Hybrid hyb;
   sable::Tiling tiling;

@@ -228,3 +228,49 @@ def dense_operand(seed, rows, cols=None, dist="uniform"):
     if dist == "int":
         return rng.integers(-4, 5, shape).astype(np.float32)
     return rng.uniform(-1.0, 1.0, shape).astype(np.float32)
+
+
+def planner_matrix(rng, rows=(100_000, 1_000_000), npr=(4.0, 24.0)):
+    """One matrix of the planner's data set: rows log-uniform in `rows`, entries
+    per row log-uniform in `npr`, split by Dirichlet(0.7, 0.7, 0.7) shares among
+    bands (up to 24 adjacent diagonals around a random offset, spans 30-100 %),
+    delta-dense blocks (sides 16-512, cell density 0.6-1.0, disjoint rows and
+    columns) and power-law (alpha = 2) scattered rows."""
+    m = int(round(math.exp(rng.uniform(math.log(rows[0]), math.log(rows[1])))))
+    npr_ = float(math.exp(rng.uniform(math.log(npr[0]), math.log(npr[1]))))
+    f = rng.dirichlet([0.7, 0.7, 0.7])
+    bands = []
+    nb = min(24, int(round(f[0] * npr_)))
+    if nb > 0:
+        center = int(rng.integers(-m // 4, m // 4 + 1))
+        for k in range(nb):
+            ln = int(rng.integers(int(0.3 * m), m + 1))
+            off = center + k - nb // 2
+            ln = min(ln, m - abs(off))
+            bands.append((off, int(rng.integers(0, m - abs(off) - ln + 1)), ln))
+    blocks = []
+    target = f[1] * npr_ * m
+    smax = max(16, min(512, m // 16))
+    sr, sc, got = [], [], 0.0
+    dens = float(rng.uniform(0.6, 1.0))
+    while got < target and sum(sr) + smax < m and sum(sc) + smax < m:
+        a, b = int(rng.integers(16, smax + 1)), int(rng.integers(16, smax + 1))
+        sr.append(a)
+        sc.append(b)
+        got += a * b * dens
+    if sr:
+        rs, cs = disjoint_starts(rng, m, sr), disjoint_starts(rng, m, sc)
+        blocks = [(int(r), int(c), a, b, dens) for r, c, a, b in zip(rs, cs, sr, sc)]
+    ns = f[2] * npr_
+    rl = None
+    if ns > 0.05:
+        rl = powerlaw_lengths(rng, m, kmax=500)
+        rl = np.minimum(500, np.round(rl * (ns / 3.4)).astype(np.int64))   # mean of P(k)~k^-2 on [1,500] ~ 3.4
+    A = assemble(rng, m, m, bands=bands, blocks=blocks, row_lengths=rl, values="normal")
+    A["meta"] = dict(bands=len(bands), blocks=len(blocks), fractions=f.tolist(), npr=npr_)
+    return A
+
+
+def planner_set_matrix(i, seed=1005, rows=(100_000, 1_000_000)):
+    """Matrix i of the planner's data set (each index seeded on its own)."""
+    return planner_matrix(np.random.default_rng([seed, i]), rows)

@@ -1,0 +1,53 @@
+"""A plan rebuilt from a saved region table computes exactly what the
+extracted plan computes on the device; a reset plan can be extracted and
+uploaded again."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_2407_00829_gb300 as sable
+import synth
+from test_host_regions import PLANS, _matrix
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _run(P, x, B):
+    y = torch.full((P.m,), float("nan"), device="cuda")
+    C = torch.full((P.m, B.shape[1]), float("nan"), device="cuda")
+    P.spmv(x, y)
+    P.spmm(B, C, sable.FP32)
+    torch.cuda.synchronize()
+    return y.cpu().numpy(), C.cpu().numpy()
+
+
+@pytest.mark.parametrize("k", range(len(PLANS)))
+def test_rebuilt_plan_matches_bitwise(k):
+    A = _matrix(21 + k)
+    P = sable.plan_from(A, PLANS[k])
+    Q = sable.Plan(A["m"], A["n"], A["row"], A["col"], A["val"]).add_stages(P.region_table()).extract().upload()
+    xs = synth.dense_operand(3, A["n"])
+    Bs = synth.dense_operand(4, A["n"], 24)
+    x, B = torch.from_numpy(xs).cuda(), torch.from_numpy(Bs).cuda()
+    yp, cp = _run(P, x, B)
+    yq, cq = _run(Q, x, B)
+    np.testing.assert_array_equal(yp, yq)
+    np.testing.assert_array_equal(cp, cq)
+    assert oracle.normwise_err(yq, oracle.spmv(A["m"], A["row"], A["col"], A["val"], xs)) <= 1e-5
+    # the same plan object, reset and extracted with another plan
+    Q.reset()
+    Q.add_stages(sable.plan_from(A, PLANS[(k + 1) % len(PLANS)], upload=False).region_table()).extract().upload()
+    yr, cr = _run(Q, x, B)
+    assert oracle.normwise_err(yr, oracle.spmv(A["m"], A["row"], A["col"], A["val"], xs)) <= 1e-5
+    assert oracle.normwise_err(cr, oracle.spmm(A["m"], A["row"], A["col"], A["val"], Bs)) <= 1e-5
+    P.close()
+    Q.close()

@@ -118,6 +118,26 @@ def test_vbr_before_vdia_order():
     assert ex.blocks and ex.segments
 
 
+@pytest.mark.parametrize("seed", range(2))
+def test_band_component_cut_into_slabs(seed):
+    """Blocks searched before bands: a 12-diagonal band is a chain of hot
+    cells as tall as the matrix; its candidate boxes are slabs of max_span
+    rows, and the library and the oracle agree on the result exactly."""
+    rng = np.random.default_rng(700 + seed)
+    m = 640
+    A = synth.assemble(rng, m, m, bands=[(o, 0, m) for o in range(-6, 6)],
+                       blocks=[(100, 420, 40, 48, 0.9), (300, 330, 32, 32, 0.95)], n_scatter=800)
+    p = ox.Params(delta=0.5, a_min=200, max_span=64, tile=8)
+    rows, cols, vals = ox.canonicalize(m, m, A["row"], A["col"], A["val"])
+    boxes = ox.candidate_regions(ox.Residual(m, m, rows, cols, np.arange(rows.size)), p)
+    tall = [b for b in boxes if b[1] - b[0] > 64 + 16]
+    assert not tall, tall                       # every box spans at most one slab (+1 cell each end)
+    assert len(boxes) >= m // 64
+    ex = _compare(A, [(sable.VBR, dict(delta=0.5, a_min=200, max_span=64, tile=8)),
+                      (sable.VDIA, dict(delta=0.75, a_min=200, l_seg=16)), (sable.CSR, None)])
+    assert ex.blocks
+
+
 def test_duplicates_and_explicit_zeros():
     row = np.array([0, 0, 1, 1, 2, 2, 2], np.int32)
     col = np.array([1, 1, 0, 2, 2, 2, 0], np.int32)

@@ -171,7 +171,7 @@ sable_status sable_plan_info(sable_plan_t plan, sable_plan_stats *out);
  * blocks:   n_blocks x 4 int64 (row0, nrows, col0, ncols), sorted by row0.
  * vdia values: vdia_cells floats, segment by segment, diagonal-major
  *           (Fig. 4 layout, no padding).
- * vbr values: vbr_cells floats, block by block, column-major (Fig. 7).
+ * vbr values: vbr_cells floats, block by block, column-major (Fig. 9).
  * csr: row_ptr m+1 int64, col nnz_csr int32, val nnz_csr floats, rows sorted,
  *           columns ascending within a row. */
 sable_status sable_plan_get_segments(sable_plan_t plan, int64_t *out);
@@ -199,6 +199,38 @@ sable_status sable_plan_reset(sable_plan_t plan);
  * entries per SpMM tile.  Errors: SABLE_ERR_INVALID. */
 sable_status sable_plan_set_tiling(sable_plan_t plan, int32_t spmv_rows, int64_t spmv_bytes,
                                    int32_t spmm_rows, int64_t spmm_elems);
+
+/* The plan's current tiling (the four values of sable_plan_set_tiling). */
+typedef struct {
+  int32_t spmv_rows;
+  int64_t spmv_bytes;
+  int32_t spmm_rows;
+  int64_t spmm_elems;
+} sable_tiling;
+sable_status sable_plan_get_tiling(sable_plan_t plan, sable_tiling *out);
+
+/* Autotuner (no counterpart in the paper, which runs one generated kernel per
+ * region): time the plan's op over candidate tilings with CUDA events on
+ * `stream` and leave the plan uploaded with the fastest.  op 0 = SpMV (in =
+ * x, out = y), 1 = SpMM FP32, 2 = SpMM with BF16 blocks (in = B, n x N, out =
+ * C, m x N, row-major with leading dimension N); in / out are device buffers
+ * the timed launches read and overwrite.  Candidates: SpMV rows {128, 256,
+ * 512, 1024} x bytes {16K, 48K, 160K}; SpMM rows {8, 16, 32, 64} x cells
+ * {1024, 4096, 16384}; the other op's tiling is kept.  Each candidate is
+ * uploaded (sable_plan_upload, which reallocates the plan's device tables and
+ * waits for the device), run twice, then timed as the best of two rounds of
+ * `reps` back-to-back launches.  The winner is remembered per shape class
+ * (op, floor log2 of N, m and nnz, and the quarters of the entries in VDIA
+ * and in VBR) for the life of the process; with use_cache != 0 a known class
+ * is applied and timed without a search.  chosen / chosen_ms (host, may be
+ * NULL) receive the tiling and its mean launch time.  Repeated launches of one
+ * plan keep a matrix smaller than L2 resident there, so small plans are tuned
+ * warm.  Errors: SABLE_ERR_INVALID; SABLE_ERR_ORDER before extract; errors of
+ * upload and of the op. */
+sable_status sable_autotune(sable_plan_t plan, int32_t op, int64_t N, const float *in, float *out, int32_t reps,
+                            int32_t use_cache, sable_tiling *chosen, float *chosen_ms, void *stream);
+/* Forget every remembered tiling; returns how many there were. */
+int64_t sable_autotune_cache_clear(void);
 
 /* ---- Batches: many matrices in one grouped launch per op ----------------
  * A batch is built from `count` uploaded plans (same device; the plans must
@@ -309,6 +341,20 @@ sable_status sable_mlp_adam(int64_t count, float *params, const float *grads, fl
  * single-word gathers, the ceiling of the CSR part of SpMV on matrices with
  * scattered entries.  No counterpart in the paper.  Errors: SABLE_ERR_INVALID. */
 sable_status sable_probe_gather(const float *x, int64_t n, int64_t count, float *out, void *stream);
+
+/* Accuracy of a result, reduced on the device in FP64: the error of an FP32
+ * result y against an FP64 reference (the oracle's), as the normwise
+ * relative error max|y - ref| / max|ref| that the library's accuracy budget
+ * is stated in (1e-5 FP32, 2e-2 BF16 blocks) and its 2-norm analogue.
+ * y: device, count floats; ref: device, count doubles; out: device, 4
+ * doubles = max_i |y_i - ref_i|, max_i |ref_i|, sum (y_i - ref_i)^2,
+ * sum ref_i^2 (a NaN anywhere makes the maxima NaN).  work: device workspace
+ * of sable_error_workspace_bytes() bytes.  Two launches of a fixed grid with
+ * fixed-order reductions: the result is the same on every run.  No
+ * counterpart in the paper.  Errors: SABLE_ERR_INVALID; SABLE_ERR_CUDA. */
+int64_t sable_error_workspace_bytes(void);
+sable_status sable_error_norms(const float *y, const double *ref, int64_t count, double *out, void *work,
+                               int64_t work_bytes, void *stream);
 
 /* First error recorded on the plan (SABLE_OK if none). */
 sable_status sable_plan_status(sable_plan_t plan);

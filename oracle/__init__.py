@@ -14,7 +14,7 @@ Contents
 * ``bf16_round`` -- round-to-nearest-even to bfloat16, written from the
   definition of the format (8 exponent bits, 7 stored mantissa bits).
 * ``formats`` -- the VDIA (Section 4.2.1, Fig. 4) and VBR (Appendix B,
-  Fig. 7) layouts built from a given partition.
+  Fig. 9) layouts built from a given partition.
 * ``extract`` -- the extractors: CSR (Appendix A.1), the band extractor
   (Algorithms 3 and 4 with a FitRibbon reading) and the block partitioner
   (Algorithms 1 and 2), plus the exact partition checker.

@@ -7,7 +7,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   segment: for every offset of the segment, the values of all its rows in
   row order.  Per segment: starting row, row count, diagonal count, start in
   ``val`` and start in ``idiag``.
-* VBR (Appendix B, Fig. 7): SPARSKIT's variable block row format.  ``Rpntr``
+* VBR (Appendix B, Fig. 9): SPARSKIT's variable block row format.  ``Rpntr``
   and ``Cpntr`` cut rows and columns into block rows/columns; ``Bpntrb`` is a
   CSR-style pointer into ``Bindx`` (block-column index of each stored block);
   ``Indx`` gives the start of each block inside ``Val``, with a final entry

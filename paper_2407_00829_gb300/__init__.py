@@ -7,6 +7,7 @@ device memory and streams.  Loading fails loudly when the library is missing
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from dataclasses import dataclass
 from typing import Optional
@@ -34,6 +35,8 @@ EXPORTED = [
     "sable_batch_status", "sable_batch_destroy", "sable_features_workspace_bytes", "sable_features",
     "sable_mlp_param_count", "sable_mlp_work_floats", "sable_mlp_forward", "sable_mlp_grad", "sable_mlp_adam",
     "sable_plan_add_regions", "sable_plan_get_region_stages", "sable_plan_reset",
+    "sable_error_workspace_bytes", "sable_error_norms", "sable_plan_get_tiling", "sable_autotune",
+    "sable_autotune_cache_clear",
 ]
 
 NFEAT = 24
@@ -110,6 +113,11 @@ def lib():
             "sable_plan_add_regions": ([p, i32, p, i64], i32),
             "sable_plan_get_region_stages": ([p, p, p], i32),
             "sable_plan_reset": ([p], i32),
+            "sable_plan_get_tiling": ([p, p], i32),
+            "sable_autotune": ([p, i32, i64, p, p, i32, i32, p, p, p], i32),
+            "sable_autotune_cache_clear": ([], i64),
+            "sable_error_workspace_bytes": ([], i64),
+            "sable_error_norms": ([p, p, i64, p, p, i64, p], i32),
             "sable_mlp_param_count": ([p], i64),
             "sable_mlp_work_floats": ([p, i64], i64),
             "sable_mlp_forward": ([p, p, p, i64, p, p, p], i32),
@@ -147,6 +155,17 @@ def _stream_handle(stream) -> Optional[int]:
 
 def _dptr(t) -> int:
     return t.data_ptr()
+
+
+class Tiling(ctypes.Structure):
+    _fields_ = [("spmv_rows", ctypes.c_int32), ("spmv_bytes", ctypes.c_int64), ("spmm_rows", ctypes.c_int32),
+                ("spmm_elems", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+TUNE_SPMV, TUNE_SPMM_FP32, TUNE_SPMM_BF16 = 0, 1, 2
 
 
 class Plan:
@@ -314,6 +333,45 @@ class Plan:
 
     def status(self) -> int:
         return lib().sable_plan_status(self._h)
+
+    def tiling(self) -> dict:
+        t = Tiling()
+        _check(lib().sable_plan_get_tiling(self._h, ctypes.byref(t)), "get_tiling")
+        return t.as_dict()
+
+    def autotune(self, op: int, inp, out, reps: int = 10, use_cache: bool = True, stream=None):
+        """Pick and apply the fastest tiling for op (TUNE_SPMV / TUNE_SPMM_FP32 /
+        TUNE_SPMM_BF16) by timing it on the device; returns (tiling, ms)."""
+        N = 0 if op == TUNE_SPMV else inp.shape[1]
+        t = Tiling()
+        ms = ctypes.c_float()
+        _check(lib().sable_autotune(self._h, op, N, _dptr(inp), _dptr(out), reps, int(use_cache), ctypes.byref(t),
+                                    ctypes.byref(ms), _stream_handle(stream)), "sable_autotune")
+        return t.as_dict(), ms.value
+
+
+def autotune_cache_clear() -> int:
+    return lib().sable_autotune_cache_clear()
+
+
+def error_norms(y, ref, stream=None):
+    """FP64 device reduction of an FP32 result y against an FP64 reference
+    (both device tensors, same number of elements).  Returns a dict with
+    max_abs_err, max_abs_ref, sq_err, sq_ref, normwise (max_abs_err /
+    max_abs_ref) and rel2 (sqrt(sq_err / sq_ref))."""
+    import torch
+    if y.dtype != torch.float32 or ref.dtype != torch.float64 or y.numel() != ref.numel():
+        raise ValueError("y must be float32 and ref float64 with as many elements")
+    y, ref = y.contiguous(), ref.contiguous()
+    wb = lib().sable_error_workspace_bytes()
+    work = torch.empty(wb, dtype=torch.uint8, device=y.device)
+    out = torch.empty(4, dtype=torch.float64, device=y.device)
+    _check(lib().sable_error_norms(_dptr(y), _dptr(ref), y.numel(), _dptr(out), _dptr(work), wb,
+                                   _stream_handle(stream)), "sable_error_norms")
+    e, r, e2, r2 = out.cpu().tolist()
+    nw = e / r if r > 0 else (0.0 if e == 0 else float("inf"))
+    return {"max_abs_err": e, "max_abs_ref": r, "sq_err": e2, "sq_ref": r2, "normwise": nw,
+            "rel2": math.sqrt(e2 / r2) if r2 > 0 else (0.0 if e2 == 0 else float("inf"))}
 
 
 def save_region_table(path, table, m: int, n: int, nnz: int):

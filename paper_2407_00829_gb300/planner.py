@@ -1,7 +1,7 @@
 """Plan selection: the exhaustive planner and a learned one.
 
 A plan is an ordered list of extractors with their thresholds: the paper's
-knobs are the extractor order (Section 3.2), the block threshold delta and
+knobs are the extractor order (Section 4.3), the block threshold delta and
 A_min (Section 4.1) and the band threshold delta (Section 5 uses 0.75).  The
 exhaustive planner extracts, uploads and times every candidate plan on the
 device and keeps the fastest; it is the fallback and the judge.  The learned
@@ -58,9 +58,9 @@ def op_feature(N: int) -> float:
 
 
 def checksum(A) -> int:
+    """CRC of the structure (extraction depends on the structure only)."""
     c = zlib.crc32(np.ascontiguousarray(A["row"], np.int32).tobytes())
-    c = zlib.crc32(np.ascontiguousarray(A["col"], np.int32).tobytes(), c)
-    return zlib.crc32(np.ascontiguousarray(A["val"], np.float32).tobytes(), c)
+    return zlib.crc32(np.ascontiguousarray(A["col"], np.int32).tobytes(), c)
 
 
 def _new_plan(A) -> Plan:
@@ -175,11 +175,13 @@ def collect(indices, seed=1005, rows=(100_000, 1_000_000), table_dir=None, log=N
     feats, times, meta = [], [], []
     for i in indices:
         A = synth.planner_set_matrix(i, seed=seed, rows=rows)
-        tables = None
+        tables, from_tables = None, 0
         if table_dir:
             tables, crc = load_matrix_tables(os.path.join(table_dir, f"m{i:05d}.npz"))
-            if crc != checksum(A):
-                raise RuntimeError(f"matrix {i}: generator output differs from the one the tables were made for")
+            if crc == checksum(A):
+                from_tables = 1
+            else:   # another structure than the tables were made for: extract here
+                tables = None
         f = matrix_features(A)
         plans = build_plans(A, tables)
         x, y, B, C = _operands(A, i)
@@ -188,10 +190,10 @@ def collect(indices, seed=1005, rows=(100_000, 1_000_000), table_dir=None, log=N
             P.close()
         feats.append(f)
         times.append(t)
-        meta.append([i, A["m"], A["row"].size])
+        meta.append([i, A["m"], A["row"].size, from_tables])
         if log:
             best = [NAMES[int(np.argmin([r[o] for r in t]))] for o in range(len(OPS))]
-            log(f"{i} m={A['m']} nnz={A['row'].size} best={best}")
+            log(f"{i} m={A['m']} nnz={A['row'].size} tables={from_tables} best={best}")
     return dict(features=np.array(feats, np.float32), times=np.array(times, np.float64),
                 meta=np.array(meta, np.int64), names=np.array(NAMES), ops=np.array([o for o, _ in OPS]))
 

@@ -1,6 +1,8 @@
-"""A plan rebuilt from a saved region table computes exactly what the
-extracted plan computes on the device; a reset plan can be extracted and
-uploaded again."""
+"""A plan rebuilt from a saved region table computes what the extracted plan
+computes on the device; a reset plan can be extracted and uploaded again.
+(The host tables of the two plans are compared bit for bit on the CPU; on the
+device the VBR part sums warp partials with shared-memory atomics, whose
+order varies from run to run, so the results agree to FP32 rounding.)"""
 import numpy as np
 import pytest
 
@@ -31,7 +33,7 @@ def _run(P, x, B):
 
 
 @pytest.mark.parametrize("k", range(len(PLANS)))
-def test_rebuilt_plan_matches_bitwise(k):
+def test_rebuilt_plan_matches(k):
     A = _matrix(21 + k)
     P = sable.plan_from(A, PLANS[k])
     Q = sable.Plan(A["m"], A["n"], A["row"], A["col"], A["val"]).add_stages(P.region_table()).extract().upload()
@@ -40,8 +42,8 @@ def test_rebuilt_plan_matches_bitwise(k):
     x, B = torch.from_numpy(xs).cuda(), torch.from_numpy(Bs).cuda()
     yp, cp = _run(P, x, B)
     yq, cq = _run(Q, x, B)
-    np.testing.assert_array_equal(yp, yq)
-    np.testing.assert_array_equal(cp, cq)
+    assert oracle.normwise_err(yq, yp) <= 1e-6
+    assert oracle.normwise_err(cq, cp) <= 1e-6
     assert oracle.normwise_err(yq, oracle.spmv(A["m"], A["row"], A["col"], A["val"], xs)) <= 1e-5
     # the same plan object, reset and extracted with another plan
     Q.reset()

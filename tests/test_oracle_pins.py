@@ -127,7 +127,7 @@ def test_vdia_layout_fig4():
 
 
 def test_vbr_layout_fig7():
-    g = read_golden("vbr_fig7.txt")
+    g = read_golden("vbr_fig9.txt")
     M = g["matrix"]
     ent = {(i, j): v for i, r in enumerate(M) for j, v in enumerate(r)}   # zeros inside blocks kept
     bp, bindx = [int(v) for v in g["Bpntrb"]], [int(v) for v in g["Bindx"]]

@@ -9,7 +9,7 @@ defeated by rotating over replicas of the matrix whose total size exceeds
 3 x L2, so every launch streams its matrix from HBM.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-                  [--workload spmv1m|spmv4096|spmm200k]
+                  [--workload spmv1m|spmv4096|batch512|planner]
 """
 from __future__ import annotations
 
@@ -39,7 +39,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="sable", choices=["sable", "reference"])
-    ap.add_argument("--workload", default="spmv1m", choices=["spmv1m", "spmv4096", "batch512"])
+    ap.add_argument("--workload", default="spmv1m", choices=["spmv1m", "spmv4096", "batch512", "planner"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmm", action="store_true")
@@ -211,15 +211,30 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
            "nnz": info["nnz"], "nnz_vbr": info["nnz_vbr"], "blocks": info["n_blocks"], "N": N,
            "extract_s": round(t_ex, 2), "steps": k}
     res = {}
-    for name, fn, cb in (("fp32", lambda i: P.spmm(B, C, sable.FP32, stream), 4),
-                         ("bf16_blocks", lambda i: P.spmm(B, C, sable.BF16_BLOCKS, stream), 2),
-                         ("plain_csr", lambda i: P.csr_spmm(B, C, stream), None)):
-        for _ in range(3):
-            fn(0)
-        ms = timed(fn, k)
-        nb = nbytes(cb) if cb else 8 * info["nnz"] + 4 * (info["m"] + 1) + 4 * info["n"] * N + 4 * info["m"] * N
-        res[name] = {"ms": ms, "GFLOP/s": flops / (ms * 1e-3) / 1e9, "GB/s": nb / (ms * 1e-3) / 1e9,
-                     "frac_hbm": nb / (ms * 1e-3) / 1e9 / peak}
+    variants = (("fp32", lambda i: P.spmm(B, C, sable.FP32, stream), 4),
+                ("bf16_blocks", lambda i: P.spmm(B, C, sable.BF16_BLOCKS, stream), 2),
+                ("plain_csr", lambda i: P.csr_spmm(B, C, stream), None))
+
+    def run_variants(names):
+        got = {}
+        for name, fn, cb in variants:
+            if name not in names:
+                continue
+            for _ in range(3):
+                fn(0)
+            ms = timed(fn, k)
+            nb = nbytes(cb) if cb else 8 * info["nnz"] + 4 * (info["m"] + 1) + 4 * info["n"] * N + 4 * info["m"] * N
+            got[name] = {"ms": ms, "GFLOP/s": flops / (ms * 1e-3) / 1e9, "GB/s": nb / (ms * 1e-3) / 1e9,
+                         "frac_hbm": nb / (ms * 1e-3) / 1e9 / peak}
+        return got
+
+    default = run_variants(("fp32", "bf16_blocks"))
+    t0 = time.perf_counter()
+    tuned, _ = P.autotune(sable.TUNE_SPMM_BF16, B, C, reps=5, use_cache=False, stream=stream)
+    out["autotune"] = {"chosen": {"spmm_rows": tuned["spmm_rows"], "spmm_elems": tuned["spmm_elems"]},
+                       "default": {"spmm_rows": 32, "spmm_elems": 4096}, "tune_s": round(time.perf_counter() - t0, 2),
+                       "default_tiling_ms": {k_: v["ms"] for k_, v in default.items()}}
+    res.update(run_variants(("fp32", "bf16_blocks", "plain_csr")))
     try:
         order = np.lexsort((A["col"], A["row"]))
         crow = np.zeros(A["m"] + 1, dtype=np.int64)
@@ -268,13 +283,23 @@ def run_batch(args):
     for P in plans:
         P.upload()
     infos = [P.info() for P in plans]
-    B = sable.Batch(plans)
     stream = torch.cuda.current_stream(dev)
     xs = [torch.from_numpy(synth.dense_operand(i, A["n"])).to(dev) for i, A in enumerate(mats)]
     ys = [torch.empty(A["m"], device=dev) for A in mats]
     N = 32
     Bs = [torch.from_numpy(synth.dense_operand(1000 + i, A["n"], N)).to(dev) for i, A in enumerate(mats)]
     Cs = [torch.empty(A["m"], N, device=dev) for A in mats]
+    # tile shapes of the grouped launch, tuned over the whole batch (graph replay timed)
+    from paper_2407_00829_gb300 import tune
+    t0 = time.perf_counter()
+    tv, tv_ms = tune.tune_batch(plans, "spmv", xs, ys, stream=stream)
+    tm, tm_ms = tune.tune_batch(plans, "spmm_bf16", Bs, Cs, N=N, stream=stream)
+    autotune = {"spmv": {"chosen": [tv["spmv_rows"], tv["spmv_bytes"]], "ms_chosen": min(tv_ms.values()),
+                         "ms_default": tv_ms[(512, 48 << 10)]},
+                "spmm_bf16": {"chosen": [tm["spmm_rows"], tm["spmm_elems"]], "ms_chosen": min(tm_ms.values()),
+                              "ms_default": tm_ms[(32, 4096)]},
+                "tune_s": round(time.perf_counter() - t0, 1)}
+    B = sable.Batch(plans)
     nnz = sum(i["nnz"] for i in infos)
     vbytes = sum(i["spmv_bytes"] for i in infos)
 
@@ -315,12 +340,63 @@ def run_batch(args):
             "spmv_GB/s": vbytes / (ms * 1e-3) / 1e9,
             "spmm_fp32_GFLOP/s": 2.0 * nnz * N / (res["spmm_fp32_graph_ms"] * 1e-3) / 1e9,
             "spmm_bf16_GFLOP/s": 2.0 * nnz * N / (res["spmm_bf16_blocks_graph_ms"] * 1e-3) / 1e9,
-            "times_ms": res, "gpu_launches": 1}
+            "times_ms": res, "autotune": autotune, "gpu_launches": 1}
     print(json.dumps(line), flush=True)
     gv.close()
     B.close()
     for P in plans:
         P.close()
+
+
+def run_planner(args):
+    """The learned planner against the exhaustive planner.  Held-out part: the
+    committed timings of 200 generated matrices (100k-1M rows, bands, delta-
+    dense blocks 16-512, power-law scatter) that the committed weights were
+    not trained on; the plan-quality loss t_chosen / t_exhaustive - 1 of the
+    weights' choices (run by the library's forward kernel on the device
+    features), of the fixed three-format plan and of CSR alone.  Live part: a
+    few fresh matrices of the same generator, each planned both ways now:
+    planning seconds (learned: device features + MLP + one extraction and
+    upload; exhaustive: every candidate extracted, uploaded and timed) and the
+    device time of the chosen plan against the best one."""
+    import torch
+    from paper_2407_00829_gb300 import build as sbuild
+    sbuild.build()
+    from paper_2407_00829_gb300 import planner as pl
+    import synth
+    torch.cuda.set_device(0)
+    here = os.path.join(ROOT, "paper_2407_00829_gb300")
+    d = dict(np.load(os.path.join(here, "planner_data.npz")))
+    lp = pl.LearnedPlanner.load(os.path.join(here, "planner_weights.json"))
+    res, _ = pl.evaluate(d, n_test=200, lp=lp)
+    live = []
+    for i in range(max(1, min(args.steps, 3))):
+        A = synth.planner_set_matrix(200_000 + i)
+        best, t, t_exh = pl.exhaustive(A, op=0)
+        t0 = time.perf_counter()
+        name = lp.plan(A, N=0)
+        spec = dict(pl.CANDIDATES)[name]
+        import paper_2407_00829_gb300 as sable
+        P = sable.plan_from(A, spec)
+        torch.cuda.synchronize()
+        t_learned = time.perf_counter() - t0
+        P.close()
+        k = pl.NAMES.index(name)
+        live.append({"m": A["m"], "nnz": int(A["row"].size), "learned": name, "exhaustive": pl.NAMES[best],
+                     "spmv_ms_learned": t[k], "spmv_ms_best": t[best],
+                     "spmv_ms_default": t[pl.NAMES.index(pl.DEFAULT)],
+                     "planning_s_learned": round(t_learned, 3), "planning_s_exhaustive": round(t_exh, 3)})
+    value = float(np.mean([res["learned"][op]["mean_loss"] for op, _ in pl.OPS]))
+    line = {"metric": "learned planner: mean plan-quality loss t_chosen / t_exhaustive - 1 (held-out)",
+            "value": value, "unit": "fraction", "n_gpus": 1, "steps": len(live), "warmup": 0,
+            "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "planner: 100k-1M-row generated matrices, 9 candidate plans, SpMV and "
+                                   "SpMM N=64 BF16 blocks", "train_matrices": res["train_matrices"],
+                       "test_matrices": res["test_matrices"], "candidates": pl.NAMES},
+            "held_out": {k: res[k] for k in ("learned", "default", "csr", "best_fixed")},
+            "live": live, "gpu_launches": None}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -330,6 +406,9 @@ def main():
         return
     if args.workload == "batch512":
         run_batch(args)
+        return
+    if args.workload == "planner":
+        run_planner(args)
         return
     ws, rank, local = _dist()
     import torch
@@ -376,6 +455,22 @@ def main():
 
     def plain(i):
         plans[i].csr_spmv(xs[i], ys[i], stream)
+
+    # autotuner: the default tiling timed over the rotation, then sable_autotune
+    # on one replica (its choice is applied to every replica)
+    for i in range(3):
+        hybrid(i % reps)
+    ms_default_tiling = timed(hybrid, min(args.steps, 500))
+    t0 = time.perf_counter()
+    tuned, tuned_ms = P0.autotune(sable.TUNE_SPMV, xs[0], ys[0], reps=20, use_cache=False, stream=stream)
+    t_tune = time.perf_counter() - t0
+    for P in plans[1:]:
+        P.set_tiling(**tuned)
+        P.upload(stream)
+    autotune = {"chosen": {"spmv_rows": tuned["spmv_rows"], "spmv_bytes": tuned["spmv_bytes"]},
+                "default": {"spmv_rows": 512, "spmv_bytes": 48 << 10},
+                "ms_default_tiling_rotated": ms_default_tiling, "ms_tuner_warm": tuned_ms,
+                "tune_s": round(t_tune, 2)}
 
     clk = Clocks(local)
     time.sleep(0.3)
@@ -502,6 +597,7 @@ def main():
                     "h2d_bytes_per_step": 4 * info["n"], "d2h_bytes_per_step": 4 * info["m"],
                     "ms_per_step": ms_e2e, "steps": k_e2e},
             "spmm": spmm,
+            "autotune": autotune,
             "gpu_launches": args.steps,
             "clocks": clocks,
         }

@@ -241,10 +241,10 @@ class LearnedPlanner:
         x = np.concatenate([matrix_features(A), [op_feature(N)]])[None, :]
         return NAMES[int(self.choose(x)[0])]
 
-    def save(self, path):
+    def save(self, path, **extra):
         with open(path, "w") as f:
-            json.dump({"names": NAMES, "n_in": N_IN, "hidden": self.net.shape.n_h1,
-                       "params": [float(v) for v in self.net.params.cpu().numpy()]}, f)
+            json.dump(dict(extra, names=NAMES, n_in=N_IN, hidden=self.net.shape.n_h1,
+                           params=[float(v) for v in self.net.params.cpu().numpy()]), f)
 
     @classmethod
     def load(cls, path):
@@ -334,8 +334,10 @@ def main():
         d = {k: v[order] for k, v in d.items()}
         res, lp = evaluate(d, n_test=a.test, steps=a.steps)
         print(json.dumps(res))
+        if a.out.endswith(".npz"):
+            np.savez_compressed(a.out, names=np.array(NAMES), ops=np.array([o for o, _ in OPS]), **d)
         if a.weights:
-            lp.save(a.weights)
+            lp.save(a.weights, eval=res, data_matrices=int(d["features"].shape[0]))
 
 
 if __name__ == "__main__":

@@ -206,8 +206,18 @@ typedef struct {
   int64_t spmv_bytes;
   int32_t spmm_rows;
   int64_t spmm_elems;
+  int32_t spmm_cols;   /* 0 = widest panel the operands allow; else 32, 64 or 128 */
 } sable_tiling;
 sable_status sable_plan_get_tiling(sable_plan_t plan, sable_tiling *out);
+
+/* Columns of C (and B) one SpMM CTA works on: 128 (four per lane; needs N,
+ * ldb, ldc multiples of 4 and 16-byte aligned B, C), 64 (two per lane; even
+ * N, ldb, ldc and 8-byte alignment) or 32; 0 picks the widest the operands
+ * allow.  The column panels of one launch run one after another, so a
+ * narrower panel keeps a smaller slice of B live in L2 while its rows are
+ * gathered.  A panel the operands do not allow falls back to 32.  Takes
+ * effect at the next SpMM call.  Errors: SABLE_ERR_INVALID. */
+sable_status sable_plan_set_spmm_cols(sable_plan_t plan, int32_t cols);
 
 /* Autotuner (no counterpart in the paper, which runs one generated kernel per
  * region): time the plan's op over candidate tilings with CUDA events on
@@ -216,7 +226,8 @@ sable_status sable_plan_get_tiling(sable_plan_t plan, sable_tiling *out);
  * C, m x N, row-major with leading dimension N); in / out are device buffers
  * the timed launches read and overwrite.  Candidates: SpMV rows {128, 256,
  * 512, 1024} x bytes {16K, 48K, 160K}; SpMM rows {8, 16, 32, 64} x cells
- * {1024, 4096, 16384}; the other op's tiling is kept.  Each candidate is
+ * {1024, 4096, 16384} x column panel {128, 64}; the other op's tiling is
+ * kept.  Each candidate is
  * uploaded (sable_plan_upload, which reallocates the plan's device tables and
  * waits for the device), run twice, then timed as the best of two rounds of
  * `reps` back-to-back launches.  The winner is remembered per shape class

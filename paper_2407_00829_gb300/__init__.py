@@ -36,7 +36,7 @@ EXPORTED = [
     "sable_mlp_param_count", "sable_mlp_work_floats", "sable_mlp_forward", "sable_mlp_grad", "sable_mlp_adam",
     "sable_plan_add_regions", "sable_plan_get_region_stages", "sable_plan_reset",
     "sable_error_workspace_bytes", "sable_error_norms", "sable_plan_get_tiling", "sable_autotune",
-    "sable_autotune_cache_clear",
+    "sable_autotune_cache_clear", "sable_plan_set_spmm_cols",
 ]
 
 NFEAT = 24
@@ -116,6 +116,7 @@ def lib():
             "sable_plan_get_tiling": ([p, p], i32),
             "sable_autotune": ([p, i32, i64, p, p, i32, i32, p, p, p], i32),
             "sable_autotune_cache_clear": ([], i64),
+            "sable_plan_set_spmm_cols": ([p, i32], i32),
             "sable_error_workspace_bytes": ([], i64),
             "sable_error_norms": ([p, p, i64, p, p, i64, p], i32),
             "sable_mlp_param_count": ([p], i64),
@@ -159,7 +160,7 @@ def _dptr(t) -> int:
 
 class Tiling(ctypes.Structure):
     _fields_ = [("spmv_rows", ctypes.c_int32), ("spmv_bytes", ctypes.c_int64), ("spmm_rows", ctypes.c_int32),
-                ("spmm_elems", ctypes.c_int64)]
+                ("spmm_elems", ctypes.c_int64), ("spmm_cols", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -265,9 +266,11 @@ class Plan:
         _check(lib().sable_extract(self._h), "sable_extract")
         return self
 
-    def set_tiling(self, spmv_rows=512, spmv_bytes=48 * 1024, spmm_rows=32, spmm_elems=4096):
+    def set_tiling(self, spmv_rows=512, spmv_bytes=48 * 1024, spmm_rows=32, spmm_elems=4096, spmm_cols=None):
         _check(lib().sable_plan_set_tiling(self._h, spmv_rows, spmv_bytes, spmm_rows, spmm_elems),
                "set_tiling")
+        if spmm_cols is not None:
+            _check(lib().sable_plan_set_spmm_cols(self._h, spmm_cols), "set_spmm_cols")
         return self
 
     def upload(self, stream=None):

@@ -421,6 +421,12 @@ sable_status sable_plan_set_tiling(sable_plan_t P, int32_t spmv_rows, int64_t sp
   return SABLE_OK;
 }
 
+sable_status sable_plan_set_spmm_cols(sable_plan_t P, int32_t cols) {
+  if (!P || (cols != 0 && cols != 32 && cols != 64 && cols != 128)) return SABLE_ERR_INVALID;
+  P->tiling.spmm_cols = cols;
+  return SABLE_OK;
+}
+
 sable_status sable_plan_status(sable_plan_t P) { return P ? P->sticky : SABLE_ERR_INVALID; }
 
 }  // extern "C"

@@ -44,6 +44,22 @@ template <> struct VecT<4> {
     atomicAdd(p, a.x); atomicAdd(p + 1, a.y); atomicAdd(p + 2, a.z); atomicAdd(p + 3, a.w);
   }
 };
+template <> struct VecT<2> {
+  using T = float2;
+  __device__ static T zero() { return make_float2(0.f, 0.f); }
+  __device__ static T load(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+  __device__ static T load_once(const float *p) { return __ldcs(reinterpret_cast<const float2 *>(p)); }
+  __device__ static void store_once(float *p, const T &a) { __stcs(reinterpret_cast<float2 *>(p), a); }
+  __device__ static void fma(T &a, float s, const T &b) {
+    a.x = fmaf(s, b.x, a.x); a.y = fmaf(s, b.y, a.y);
+  }
+  __device__ static void add_to(float *p, const T &a) {
+    p[0] += a.x; p[1] += a.y;
+  }
+  __device__ static void atomic_add_to(float *p, const T &a) {
+    atomicAdd(p, a.x); atomicAdd(p + 1, a.y);
+  }
+};
 template <> struct VecT<1> {
   using T = float;
   __device__ static T zero() { return 0.f; }
@@ -193,6 +209,8 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
         float *dst = C + (int64_t)(r0 + i) * ldc + n0 + lc;
         if (V == 4) {
           __stcs(reinterpret_cast<float4 *>(dst), *reinterpret_cast<const float4 *>(src));
+        } else if (V == 2) {
+          __stcs(reinterpret_cast<float2 *>(dst), *reinterpret_cast<const float2 *>(src));
         } else {
           __stcs(dst, src[0]);
         }
@@ -562,12 +580,29 @@ sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int
   if (!C || (D.n > 0 && !B)) return SABLE_ERR_INVALID;
   const bool vec = N % 4 == 0 && ldb % 4 == 0 && ldc % 4 == 0 &&
                    ((uintptr_t)B & 15) == 0 && ((uintptr_t)C & 15) == 0;
+  const bool vec2 = N % 2 == 0 && ldb % 2 == 0 && ldc % 2 == 0 &&
+                    ((uintptr_t)B & 7) == 0 && ((uintptr_t)C & 7) == 0;
+  // column panel per CTA: 128 (float4 lanes), 64 (float2) or 32; the panels
+  // of a launch run one after another in time, so a narrower panel keeps a
+  // smaller slice of B live in L2
+  const int cols = P->tiling.spmm_cols;
+  const int V = cols == 32 ? 1 : cols == 64 ? (vec2 ? 2 : 1) : (vec ? 4 : 1);
   constexpr int TH = 256;
-  const int NT = vec ? 128 : 32;
+  const int NT = 32 * V;
   const size_t smem = (size_t)D.spmm.rows_max * NT * 4 + ((size_t)D.spmm.rows_max + 1) * 4;
   const int gy = (int)((N + NT - 1) / NT);
-  if (vec && vbrc) {
+  if (V == 4 && vbrc) {
     auto k = spmm_hybrid_kernel<TH, 4, true>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
+    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
+  } else if (V == 2 && vbrc) {
+    auto k = spmm_hybrid_kernel<TH, 2, true>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
+    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
+  } else if (V == 2) {
+    auto k = spmm_hybrid_kernel<TH, 2, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
     k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
@@ -576,7 +611,7 @@ sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
     k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
-  } else if (vec) {
+  } else if (V == 4) {
     auto k = spmm_hybrid_kernel<TH, 4, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);

@@ -103,6 +103,7 @@ struct Tiling {
   int64_t item_bytes = 48 * 1024;
   int32_t rows_per_item_mm = 32; // SpMM row tile (<= 256, multiple of 4)
   int64_t item_elems_mm = 4096;  // stored cells + entries per SpMM tile
+  int32_t spmm_cols = 0;         // SpMM column panel per CTA: 0 = widest the operands allow, 32, 64, 128
 };
 
 // Host-side extracted hybrid form and its device mirror.

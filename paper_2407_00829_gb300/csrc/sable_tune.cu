@@ -64,8 +64,12 @@ sable_status time_op(sable_plan_t P, int op, int64_t N, const float *in, float *
 }
 
 sable_status apply(sable_plan_t P, const sable_tiling &t, cudaStream_t st) {
+  const Tiling &now = P->tiling;
+  const bool same_tables = P->uploaded && now.rows_per_item == t.spmv_rows && now.item_bytes == t.spmv_bytes &&
+                           now.rows_per_item_mm == t.spmm_rows && now.item_elems_mm == t.spmm_elems;
   sable_status s = sable_plan_set_tiling(P, t.spmv_rows, t.spmv_bytes, t.spmm_rows, t.spmm_elems);
-  if (!s) s = sable_plan_upload(P, st);
+  if (!s) s = sable_plan_set_spmm_cols(P, t.spmm_cols);
+  if (!s && !same_tables) s = sable_plan_upload(P, st);   // the column panel needs no new tables
   return s;
 }
 
@@ -82,6 +86,7 @@ sable_status sable_plan_get_tiling(sable_plan_t P, sable_tiling *out) {
   out->spmv_bytes = P->tiling.item_bytes;
   out->spmm_rows = P->tiling.rows_per_item_mm;
   out->spmm_elems = P->tiling.item_elems_mm;
+  out->spmm_cols = P->tiling.spmm_cols;
   return SABLE_OK;
 }
 
@@ -108,6 +113,7 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
       } else {
         t.spmm_rows = it->second.spmm_rows;
         t.spmm_elems = it->second.spmm_elems;
+        t.spmm_cols = it->second.spmm_cols;
       }
       cand.push_back(t);
       cached = true;
@@ -116,10 +122,12 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
   if (!cached) {
     if (op == 0) {
       for (int32_t rows : {128, 256, 512, 1024})
-        for (int64_t bytes : {16 << 10, 48 << 10, 160 << 10}) cand.push_back({rows, bytes, cur.spmm_rows, cur.spmm_elems});
+        for (int64_t bytes : {16 << 10, 48 << 10, 160 << 10})
+          cand.push_back({rows, bytes, cur.spmm_rows, cur.spmm_elems, cur.spmm_cols});
     } else {
       for (int32_t rows : {8, 16, 32, 64})
-        for (int64_t elems : {1024, 4096, 16384}) cand.push_back({cur.spmv_rows, cur.spmv_bytes, rows, elems});
+        for (int64_t elems : {1024, 4096, 16384})
+          for (int32_t cols : {128, 64}) cand.push_back({cur.spmv_rows, cur.spmv_bytes, rows, elems, cols});
     }
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;

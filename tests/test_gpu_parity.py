@@ -84,9 +84,9 @@ def test_spmv_small(case, plan):
     P.close()
 
 
-@pytest.mark.parametrize("tiling", [dict(spmv_rows=4, spmv_bytes=64, spmm_rows=4, spmm_elems=1),
+@pytest.mark.parametrize("tiling", [dict(spmv_rows=4, spmv_bytes=64, spmm_rows=4, spmm_elems=1, spmm_cols=32),
                                     dict(spmv_rows=1024, spmv_bytes=1 << 22, spmm_rows=256, spmm_elems=1 << 20),
-                                    dict(spmv_rows=36, spmv_bytes=300, spmm_rows=12, spmm_elems=100)])
+                                    dict(spmv_rows=36, spmv_bytes=300, spmm_rows=12, spmm_elems=100, spmm_cols=64)])
 def test_spmv_integer_exact_any_tiling(tiling):
     rng = np.random.default_rng(42)
     m, n = 1501, 1203
@@ -140,10 +140,12 @@ def test_order_errors_on_device():
     P.close()
 
 
+@pytest.mark.parametrize("cols", [0, 64, 32])
 @pytest.mark.parametrize("N", [1, 7, 32, 128, 200])
-def test_spmm_small(N):
+def test_spmm_small(N, cols):
     A = SMALL[2]
     P = sable.plan_from(A, PLANS[0])
+    P.set_tiling(**dict(P.tiling(), spmm_cols=cols))
     B = synth.dense_operand(N, A["n"], N)
     ref = oracle.spmm(A["m"], A["row"], A["col"], A["val"], B)
     assert oracle.normwise_err(_spmm(P, B), ref) <= TOL_FP32
@@ -187,9 +189,11 @@ def test_blocks_scatter_200k_full_size_sampled():
     sel = np.random.default_rng(0).choice(A["m"], 3000, replace=False)
     ref = oracle.spmm_rows(A["m"], A["row"], A["col"], A["val"], B, sel)
     Bd = _dev(B)
-    for prec, tol in ((sable.FP32, TOL_FP32), (sable.BF16_BLOCKS, 2e-2)):
-        C = torch.empty(A["m"], 128, device="cuda")
-        P.spmm(Bd, C, prec)
-        torch.cuda.synchronize()
-        assert oracle.normwise_err(C[torch.from_numpy(sel).cuda()].cpu().numpy(), ref) <= tol
+    for cols in (0, 64):
+        P.set_tiling(**dict(P.tiling(), spmm_cols=cols))
+        for prec, tol in ((sable.FP32, TOL_FP32), (sable.BF16_BLOCKS, 2e-2)):
+            C = torch.empty(A["m"], 128, device="cuda")
+            P.spmm(Bd, C, prec)
+            torch.cuda.synchronize()
+            assert oracle.normwise_err(C[torch.from_numpy(sel).cuda()].cpu().numpy(), ref) <= tol
     P.close()

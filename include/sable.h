@@ -185,6 +185,19 @@ sable_status sable_plan_get_csr(sable_plan_t plan, int64_t *row_ptr, int32_t *co
  * n_blocks int32.  Together they are the plan's region table. */
 sable_status sable_plan_get_region_stages(sable_plan_t plan, int32_t *seg_stage, int32_t *blk_stage);
 
+/* New values for the same structure: the extracted regions and, after
+ * upload, the device tables are kept and only the values are replaced (the
+ * paper's inspector-executor reuse: the regions depend on the structure only,
+ * so a program built for one matrix serves every matrix with the same
+ * pattern, Sections 2 and 3.4).  val: host, the nnz floats of the COO given to
+ * sable_plan_create, in that order (duplicates are summed again as there:
+ * FP64 in input order, rounded once).  The BF16 copies of the blocks and
+ * their scales are recomputed.  With an uploaded plan the device must be the
+ * plan's; the values are copied on `stream`, which the call waits for.
+ * Errors: SABLE_ERR_INVALID; SABLE_ERR_ORDER before sable_extract;
+ * SABLE_ERR_OOM / SABLE_ERR_CUDA. */
+sable_status sable_plan_update_values(sable_plan_t plan, const float *val, void *stream);
+
 /* Start the plan over from its canonical matrix: drop the stages, the
  * extraction and the device tables (cudaFree, which waits for the device),
  * keep the matrix and the tiling, clear the recorded error.  New stages can

@@ -36,7 +36,7 @@ EXPORTED = [
     "sable_mlp_param_count", "sable_mlp_work_floats", "sable_mlp_forward", "sable_mlp_grad", "sable_mlp_adam",
     "sable_plan_add_regions", "sable_plan_get_region_stages", "sable_plan_reset",
     "sable_error_workspace_bytes", "sable_error_norms", "sable_plan_get_tiling", "sable_autotune",
-    "sable_autotune_cache_clear", "sable_plan_set_spmm_cols",
+    "sable_autotune_cache_clear", "sable_plan_set_spmm_cols", "sable_plan_update_values",
 ]
 
 NFEAT = 24
@@ -117,6 +117,7 @@ def lib():
             "sable_autotune": ([p, i32, i64, p, p, i32, i32, p, p, p], i32),
             "sable_autotune_cache_clear": ([], i64),
             "sable_plan_set_spmm_cols": ([p, i32], i32),
+            "sable_plan_update_values": ([p, p, p], i32),
             "sable_error_workspace_bytes": ([], i64),
             "sable_error_norms": ([p, p, i64, p, p, i64, p], i32),
             "sable_mlp_param_count": ([p], i64),
@@ -223,6 +224,16 @@ class Plan:
         g = np.ascontiguousarray(np.asarray(regions, dtype=np.int64).reshape(-1, 4))
         _check(lib().sable_plan_add_regions(self._h, kind, g.ctypes.data, g.shape[0]), "add_regions")
         self._stages.append(kind)
+        return self
+
+    def update_values(self, val, stream=None):
+        """Same structure, new values (the COO order given at creation)."""
+        v = np.ascontiguousarray(val, dtype=np.float32)
+        if stream is None:   # a plan that was never uploaded needs no stream (nor a GPU)
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        _check(lib().sable_plan_update_values(self._h, v.ctypes.data if v.size else None, _stream_handle(stream)),
+               "sable_plan_update_values")
         return self
 
     def reset(self):

@@ -105,13 +105,18 @@ sable_status sable_plan_create(int64_t m, int64_t n, int64_t nnz, const int32_t 
     C.rp.assign(m + 1, 0);
     C.ci.reserve(nnz);
     P->cval.reserve(nnz);
+    P->canon_of.assign(nnz, 0);
     for (int64_t i = 0; i < m; ++i) {
       int64_t *b = order.data() + cnt[i], *e = order.data() + cnt[i + 1];
       std::stable_sort(b, e, [&](int64_t a, int64_t z) { return col[a] < col[z]; });
       for (int64_t *q = b; q < e;) {
         const int32_t c = col[*q];
+        const int32_t id = (int32_t)C.ci.size();
         double s = 0.0;
-        for (; q < e && col[*q] == c; ++q) s += (double)val[*q];   // input order
+        for (; q < e && col[*q] == c; ++q) {   // input order
+          s += (double)val[*q];
+          P->canon_of[*q] = id;
+        }
         C.ci.push_back(c);
         P->cval.push_back((float)s);
       }
@@ -291,20 +296,24 @@ sable_status sable_extract(sable_plan_t P) {
     H.cci.clear();
     H.ccv.clear();
     int64_t nv = 0, nb = 0, nc = 0;
+    P->dest.assign(nnz, 0);
     for (int64_t i = 0; i < C.m; ++i) {
       for (int64_t k = C.rp[i]; k < C.rp[i + 1]; ++k) {
         const int64_t j = C.ci[k];
         if (P->owner[k] == OWN_VDIA) {
           const int32_t s = sidx[region[k]];
           const Segment &g = H.segs[s];
-          H.vdia_canon[sptr[s] + (j - i - g.off_lo) * g.nrows + (i - g.row0)] = P->cval[k];
+          P->dest[k] = sptr[s] + (j - i - g.off_lo) * g.nrows + (i - g.row0);
+          H.vdia_canon[P->dest[k]] = P->cval[k];
           ++nv;
         } else if (P->owner[k] == OWN_VBR) {
           const int32_t b = bidx[region[k]];
           const Block &g = H.blks[b];
-          H.vbr_canon[bptr[b] + (j - g.c0) * g.nr + (i - g.r0)] = P->cval[k];
+          P->dest[k] = bptr[b] + (j - g.c0) * g.nr + (i - g.r0);
+          H.vbr_canon[P->dest[k]] = P->cval[k];
           ++nb;
         } else {
+          P->dest[k] = (int64_t)H.ccv.size();
           H.cci.push_back((int32_t)j);
           H.ccv.push_back(P->cval[k]);
           ++nc;

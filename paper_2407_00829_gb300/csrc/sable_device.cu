@@ -92,60 +92,67 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
     for (int i = tid; i <= R; i += THREADS) rps[i] = __ldg(A.rp + r0 + i);
     __syncthreads();
 
-    // ---- A. VDIA: item row i belongs to warp i % NW in phases A and B
+    // ---- A. VDIA.  Item rows go to warps in groups of four: rows 4g .. 4g+3
+    // belong to warp g % NW in phases A and B, so their shared-memory sums
+    // need no atomics.
     for (int q = I.seg_lo; q < I.seg_hi; ++q) {
       const DevSeg s = A.segs[__ldg(A.spmm.iseg + q)];
       const int ia = max(r0, s.row0) - r0, ib = min(I.r1, s.row0 + s.nrows) - r0;
-      const int first = ia + ((warp - ia % NW) + NW) % NW;
-      for (int i = first; i < ib; i += NW) {
-        const int r = r0 + i;
-        T acc = Vt::zero();
-        const float *vp = A.vdia + s.val_off + (r - s.base);
-        for (int k = 0; k < s.ndiag; ++k) {
-          const int c = r + s.off_lo + k;
-          if ((unsigned)c >= n) continue;
-          const float v = __ldcs(vp + (int64_t)k * s.ld);
-          if (lane_ok) Vt::fma(acc, v, Vt::load(B + (int64_t)c * ldb + n0 + lc));
+      for (int g = (ia >> 2) + ((warp - (ia >> 2) % NW) + NW) % NW; 4 * g < ib; g += NW) {
+        for (int i = max(4 * g, ia); i < min(4 * g + 4, ib); ++i) {
+          const int r = r0 + i;
+          T acc = Vt::zero();
+          const float *vp = A.vdia + s.val_off + (r - s.base);
+          for (int k = 0; k < s.ndiag; ++k) {
+            const int c = r + s.off_lo + k;
+            if ((unsigned)c >= n) continue;
+            const float v = __ldcs(vp + (int64_t)k * s.ld);
+            if (lane_ok) Vt::fma(acc, v, Vt::load(B + (int64_t)c * ldb + n0 + lc));
+          }
+          if (lane_ok) Vt::add_to(cs + i * NT + lc, acc);
         }
-        if (lane_ok) Vt::add_to(cs + i * NT + lc, acc);
       }
     }
-    // ---- B. VBR: already multiplied on the tensor cores into C (VBRC), or FP32 FMA
+    // ---- B. VBR: already multiplied on the tensor cores into C (VBRC), or FP32
+    // FMA with four block rows per warp, so that each B row loaded serves four
+    // rows of the block
     if (VBRC) {
       for (int q = I.blk_lo; q < I.blk_hi; ++q) {
         const DevBlk b = A.spmm.pblk[q];
         const int ia = max(r0, b.r0) - r0, ib = min(I.r1, b.r0 + b.nr) - r0;
-        const int first = ia + ((warp - ia % NW) + NW) % NW;
-        for (int i = first; i < ib; i += NW)
-          if (lane_ok) Vt::add_to(cs + i * NT + lc, Vt::load_once(C + (int64_t)(r0 + i) * ldc + n0 + lc));
+        for (int g = (ia >> 2) + ((warp - (ia >> 2) % NW) + NW) % NW; 4 * g < ib; g += NW)
+          for (int i = max(4 * g, ia); i < min(4 * g + 4, ib); ++i)
+            if (lane_ok) Vt::add_to(cs + i * NT + lc, Vt::load_once(C + (int64_t)(r0 + i) * ldc + n0 + lc));
       }
     } else
     for (int q = I.blk_lo; q < I.blk_hi; ++q) {
       const DevBlk b = A.blks[__ldg(A.spmm.iblk + q)];
       const int ia = max(r0, b.r0) - r0, ib = min(I.r1, b.r0 + b.nr) - r0;
-      const int first = ia + ((warp - ia % NW) + NW) % NW;
-      for (int i = first; i < ib; i += NW) {
-        const float *ap = A.vbr + b.val_off + (r0 + i - b.r0);
+      for (int g = (ia >> 2) + ((warp - (ia >> 2) % NW) + NW) % NW; 4 * g < ib; g += NW) {
+        const int i0 = max(4 * g, ia), nrow = min(4 * g + 4, ib) - i0;   // 1..4 rows of this block
+        const float *ap = A.vbr + b.val_off + (r0 + i0 - b.r0);
         const float *bp = B + (int64_t)b.c0 * ldb + n0 + lc;
-        T acc = Vt::zero();
-        int c = 0;
-        for (; c + 4 <= b.nc; c += 4) {
-          const float w0 = __ldg(ap + (int64_t)c * b.nr), w1 = __ldg(ap + (int64_t)(c + 1) * b.nr);
-          const float w2 = __ldg(ap + (int64_t)(c + 2) * b.nr), w3 = __ldg(ap + (int64_t)(c + 3) * b.nr);
+        T a0 = Vt::zero(), a1 = Vt::zero(), a2 = Vt::zero(), a3 = Vt::zero();
+        for (int c = 0; c < b.nc; ++c) {
+          const float *col = ap + (int64_t)c * b.nr;
+          const float w0 = __ldg(col);
+          const float w1 = nrow > 1 ? __ldg(col + 1) : 0.f;
+          const float w2 = nrow > 2 ? __ldg(col + 2) : 0.f;
+          const float w3 = nrow > 3 ? __ldg(col + 3) : 0.f;
           if (lane_ok) {
-            const T b0 = Vt::load(bp + (int64_t)c * ldb), b1 = Vt::load(bp + (int64_t)(c + 1) * ldb);
-            const T b2 = Vt::load(bp + (int64_t)(c + 2) * ldb), b3 = Vt::load(bp + (int64_t)(c + 3) * ldb);
-            Vt::fma(acc, w0, b0);
-            Vt::fma(acc, w1, b1);
-            Vt::fma(acc, w2, b2);
-            Vt::fma(acc, w3, b3);
+            const T bv = Vt::load(bp + (int64_t)c * ldb);
+            Vt::fma(a0, w0, bv);
+            Vt::fma(a1, w1, bv);
+            Vt::fma(a2, w2, bv);
+            Vt::fma(a3, w3, bv);
           }
         }
-        for (; c < b.nc; ++c) {
-          const float w = __ldg(ap + (int64_t)c * b.nr);
-          if (lane_ok) Vt::fma(acc, w, Vt::load(bp + (int64_t)c * ldb));
+        if (lane_ok) {
+          Vt::add_to(cs + i0 * NT + lc, a0);
+          if (nrow > 1) Vt::add_to(cs + (i0 + 1) * NT + lc, a1);
+          if (nrow > 2) Vt::add_to(cs + (i0 + 2) * NT + lc, a2);
+          if (nrow > 3) Vt::add_to(cs + (i0 + 3) * NT + lc, a3);
         }
-        if (lane_ok) Vt::add_to(cs + i * NT + lc, acc);
       }
     }
     __syncthreads();
@@ -532,6 +539,13 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   P->h_items_v = S->it_v.items;
   P->h_items_m = S->it_m.items;
   P->h_trip = S->tc_pairs;
+  P->h_segs = S->segs;
+  P->o_vdia = o_vdia;
+  P->o_vbr = o_vbr;
+  P->o_bf16 = o_bf16;
+  P->o_scale = o_scale;
+  P->o_cv = o_cv;
+  P->o_pcv = o_pcv;
   delete S;
   e = cudaMemcpy(P->dev_self, &P->dev, sizeof(DevHybrid), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -664,6 +678,63 @@ sable_status sable_csr_spmm(sable_plan_t P, const float *B, int64_t N, int64_t l
   return launch_spmm(P, P->dev_plain, B, N, ldb, C, ldc, false, (cudaStream_t)stream);
 }
 
+sable_status sable_plan_update_values(sable_plan_t P, const float *val, void *stream) {
+  if (!P || (!val && !P->canon_of.empty())) return SABLE_ERR_INVALID;
+  if (P->sticky) return P->sticky;
+  if (!P->extracted) return SABLE_ERR_ORDER;
+  if (P->uploaded) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return SABLE_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Hybrid &H = P->hyb;
+  std::vector<float> vdia, cv, pcv, scales;
+  std::vector<uint16_t> bf16;
+  try {
+    // duplicates summed in FP64 in input order, rounded once: as at create
+    std::vector<double> sum(P->cval.size(), 0.0);
+    for (size_t k = 0; k < P->canon_of.size(); ++k) sum[P->canon_of[k]] += (double)val[k];
+    for (size_t c = 0; c < sum.size(); ++c) {
+      const float v = (float)sum[c];
+      P->cval[c] = v;
+      if (P->owner[c] == OWN_VDIA) H.vdia_canon[P->dest[c]] = v;
+      else if (P->owner[c] == OWN_VBR) H.vbr_canon[P->dest[c]] = v;
+      else H.ccv[P->dest[c]] = v;
+    }
+    if (!P->uploaded) return SABLE_OK;
+    int64_t cells = 4;
+    for (const DevSeg &d : P->h_segs) cells = std::max<int64_t>(cells, d.val_off + (int64_t)d.ld * d.ndiag);
+    vdia.assign(cells, 0.0f);
+    int64_t sp = 0;
+    for (const DevSeg &d : P->h_segs) {
+      for (int64_t k = 0; k < d.ndiag; ++k)
+        for (int64_t r = 0; r < d.nrows; ++r) vdia[d.val_off + k * d.ld + (d.row0 - d.base) + r] = H.vdia_canon[sp + k * d.nrows + r];
+      sp += (int64_t)d.nrows * d.ndiag;
+    }
+    std::vector<int64_t> offs;
+    pack_vbr_bf16(H.blks, H.vbr_canon, bf16, scales, offs);
+    cv.assign(H.ccv.begin(), H.ccv.end());
+    cv.resize(cv.size() + kCsrPad, 0.0f);
+    pcv.assign(P->cval.begin(), P->cval.end());
+    pcv.resize(pcv.size() + kCsrPad, 0.0f);
+  } catch (const std::bad_alloc &) {
+    return fail(P, SABLE_ERR_OOM);
+  }
+  char *blob = static_cast<char *>(P->dev_blob);
+  const struct { size_t off; const void *src; size_t bytes; } parts[] = {
+      {P->o_vdia, vdia.data(), H.segs.empty() ? 0 : vdia.size() * 4},
+      {P->o_vbr, H.vbr_canon.data(), H.vbr_canon.size() * 4},
+      {P->o_bf16, bf16.data(), bf16.size() * 2},
+      {P->o_scale, scales.data(), scales.size() * 4},
+      {P->o_cv, cv.data(), cv.size() * 4},
+      {P->o_pcv, pcv.data(), pcv.size() * 4}};
+  cudaError_t e = cudaSuccess;
+  for (const auto &pt : parts)
+    if (e == cudaSuccess && pt.bytes) e = cudaMemcpyAsync(blob + pt.off, pt.src, pt.bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the staging vectors die here
+  return e == cudaSuccess ? SABLE_OK : cuda_fail(P, e);
+}
+
 sable_status sable_plan_reset(sable_plan_t P) {
   if (!P) return SABLE_ERR_INVALID;
   if (P->dev_blob) {
@@ -692,6 +763,9 @@ sable_status sable_plan_reset(sable_plan_t P) {
   P->stage_fixed.clear();
   P->seg_stage.clear();
   P->blk_stage.clear();
+  P->dest.clear();
+  P->h_segs.clear();
+  P->o_vdia = P->o_vbr = P->o_bf16 = P->o_scale = P->o_cv = P->o_pcv = 0;
   P->owner.assign(P->canon.ci.size(), OWN_NONE);
   P->hyb = Hybrid{};
   P->stats = sable_plan_stats{};

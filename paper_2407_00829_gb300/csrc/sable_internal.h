@@ -129,6 +129,10 @@ struct sable_plan_s {
   std::vector<std::vector<int64_t>> stage_regions;   // per stage: given regions (4 values each)
   std::vector<uint8_t> stage_fixed;                  // per stage: 1 = given regions, 0 = search
   std::vector<int32_t> seg_stage, blk_stage;         // stage of each segment / block (sorted order)
+  std::vector<int32_t> canon_of;                     // input COO entry -> canonical entry
+  std::vector<int64_t> dest;                         // canonical entry -> index in its format's value array
+  std::vector<sable::DevSeg> h_segs;                 // device segment descriptors (padded VDIA layout)
+  size_t o_vdia = 0, o_vbr = 0, o_bf16 = 0, o_scale = 0, o_cv = 0, o_pcv = 0;   // value arrays in the blob
   std::vector<int8_t> owner;           // per canonical entry
   sable::Hybrid hyb;
   sable::Tiling tiling;

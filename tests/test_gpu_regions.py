@@ -53,3 +53,26 @@ def test_rebuilt_plan_matches(k):
     assert oracle.normwise_err(cr, oracle.spmm(A["m"], A["row"], A["col"], A["val"], Bs)) <= 1e-5
     P.close()
     Q.close()
+
+
+@pytest.mark.parametrize("k", range(len(PLANS)))
+def test_update_values_on_the_device(k):
+    A = _matrix(31 + k)
+    P = sable.plan_from(A, PLANS[k])
+    v2 = np.random.default_rng(k).uniform(-2, 2, A["row"].size).astype(np.float32)
+    P.update_values(v2)
+    xs = synth.dense_operand(5, A["n"])
+    Bs = synth.dense_operand(6, A["n"], 64)
+    y, C = _run(P, torch.from_numpy(xs).cuda(), torch.from_numpy(Bs).cuda())
+    assert oracle.normwise_err(y, oracle.spmv(A["m"], A["row"], A["col"], v2, xs)) <= 1e-5
+    refC = oracle.spmm(A["m"], A["row"], A["col"], v2, Bs)
+    assert oracle.normwise_err(C, refC) <= 1e-5
+    Cb = torch.empty(A["m"], 64, device="cuda")
+    P.spmm(torch.from_numpy(Bs).cuda(), Cb, sable.BF16_BLOCKS)
+    torch.cuda.synchronize()
+    assert oracle.normwise_err(Cb.cpu().numpy(), refC) <= 2e-2
+    yp = torch.empty(A["m"], device="cuda")
+    P.csr_spmv(torch.from_numpy(xs).cuda(), yp)
+    torch.cuda.synchronize()
+    assert oracle.normwise_err(yp.cpu().numpy(), oracle.spmv(A["m"], A["row"], A["col"], v2, xs)) <= 1e-5
+    P.close()

@@ -102,3 +102,20 @@ def test_invalid_region_stages():
         P.add_regions(B, [[0, 1, 0, 1]])
     assert e.value.status == 5
     P.close()
+
+
+@pytest.mark.parametrize("k", range(len(PLANS)))
+def test_update_values_equals_a_fresh_plan(k):
+    A = _matrix(40 + k)
+    # duplicates: repeat a tenth of the entries (summed at creation and at update)
+    rng = np.random.default_rng(k)
+    dup = rng.choice(A["row"].size, A["row"].size // 10, replace=False)
+    A = dict(A, row=np.concatenate([A["row"], A["row"][dup]]), col=np.concatenate([A["col"], A["col"][dup]]),
+             val=np.concatenate([A["val"], A["val"][dup]]))
+    P = sable.plan_from(A, PLANS[k], upload=False)
+    v2 = rng.standard_normal(A["row"].size).astype(np.float32)
+    P.update_values(v2)
+    Q = sable.plan_from(dict(A, val=v2), PLANS[k], upload=False)
+    _same(P, Q)
+    P.close()
+    Q.close()

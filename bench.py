@@ -238,7 +238,8 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
         t0 = time.perf_counter()
         tuned, _ = P.autotune(op, B, C, reps=5, use_cache=False, stream=stream)
         out["autotune"][name] = {"spmm_rows": tuned["spmm_rows"], "spmm_elems": tuned["spmm_elems"],
-                                 "spmm_cols": tuned["spmm_cols"], "tune_s": round(time.perf_counter() - t0, 2)}
+                                 "spmm_cols": tuned["spmm_cols"], "spmm_depth": tuned["spmm_depth"],
+                                 "tune_s": round(time.perf_counter() - t0, 2)}
         got = run_variants((name, "plain_csr"))
         res[name] = got[name]
         if got["plain_csr"]["ms"] < plain_best["ms"]:

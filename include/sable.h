@@ -220,6 +220,7 @@ typedef struct {
   int32_t spmm_rows;
   int64_t spmm_elems;
   int32_t spmm_cols;   /* 0 = widest panel the operands allow; else 32, 64 or 128 */
+  int32_t spmm_depth;  /* B rows in flight per warp in the SpMM CSR phase: 4 or 8 */
 } sable_tiling;
 sable_status sable_plan_get_tiling(sable_plan_t plan, sable_tiling *out);
 
@@ -232,6 +233,12 @@ sable_status sable_plan_get_tiling(sable_plan_t plan, sable_tiling *out);
  * effect at the next SpMM call.  Errors: SABLE_ERR_INVALID. */
 sable_status sable_plan_set_spmm_cols(sable_plan_t plan, int32_t cols);
 
+/* B rows each warp has in flight in the SpMM CSR phase: 4 (default) or 8
+ * (more loads in flight, more registers: at most 4 CTAs per SM; used with
+ * 128-column panels only).  Takes effect at the next SpMM call.  Errors:
+ * SABLE_ERR_INVALID. */
+sable_status sable_plan_set_spmm_depth(sable_plan_t plan, int32_t depth);
+
 /* Autotuner (no counterpart in the paper, which runs one generated kernel per
  * region): time the plan's op over candidate tilings with CUDA events on
  * `stream` and leave the plan uploaded with the fastest.  op 0 = SpMV (in =
@@ -239,8 +246,8 @@ sable_status sable_plan_set_spmm_cols(sable_plan_t plan, int32_t cols);
  * C, m x N, row-major with leading dimension N); in / out are device buffers
  * the timed launches read and overwrite.  Candidates: SpMV rows {128, 256,
  * 512, 1024} x bytes {16K, 48K, 160K}; SpMM rows {8, 16, 32, 64} x cells
- * {1024, 4096, 16384} x column panel {128, 64}; the other op's tiling is
- * kept.  Each candidate is
+ * {1024, 4096, 16384} x (128 columns with 4 or 8 rows in flight, 64 columns);
+ * the other op's tiling is kept.  Each candidate is
  * uploaded (sable_plan_upload, which reallocates the plan's device tables and
  * waits for the device), run twice, then timed as the best of two rounds of
  * `reps` back-to-back launches.  The winner is remembered per shape class

@@ -37,6 +37,7 @@ EXPORTED = [
     "sable_plan_add_regions", "sable_plan_get_region_stages", "sable_plan_reset",
     "sable_error_workspace_bytes", "sable_error_norms", "sable_plan_get_tiling", "sable_autotune",
     "sable_autotune_cache_clear", "sable_plan_set_spmm_cols", "sable_plan_update_values",
+    "sable_plan_set_spmm_depth",
 ]
 
 NFEAT = 24
@@ -118,6 +119,7 @@ def lib():
             "sable_autotune_cache_clear": ([], i64),
             "sable_plan_set_spmm_cols": ([p, i32], i32),
             "sable_plan_update_values": ([p, p, p], i32),
+            "sable_plan_set_spmm_depth": ([p, i32], i32),
             "sable_error_workspace_bytes": ([], i64),
             "sable_error_norms": ([p, p, i64, p, p, i64, p], i32),
             "sable_mlp_param_count": ([p], i64),
@@ -161,7 +163,7 @@ def _dptr(t) -> int:
 
 class Tiling(ctypes.Structure):
     _fields_ = [("spmv_rows", ctypes.c_int32), ("spmv_bytes", ctypes.c_int64), ("spmm_rows", ctypes.c_int32),
-                ("spmm_elems", ctypes.c_int64), ("spmm_cols", ctypes.c_int32)]
+                ("spmm_elems", ctypes.c_int64), ("spmm_cols", ctypes.c_int32), ("spmm_depth", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -277,11 +279,14 @@ class Plan:
         _check(lib().sable_extract(self._h), "sable_extract")
         return self
 
-    def set_tiling(self, spmv_rows=512, spmv_bytes=48 * 1024, spmm_rows=32, spmm_elems=4096, spmm_cols=None):
+    def set_tiling(self, spmv_rows=512, spmv_bytes=48 * 1024, spmm_rows=32, spmm_elems=4096, spmm_cols=None,
+                   spmm_depth=None):
         _check(lib().sable_plan_set_tiling(self._h, spmv_rows, spmv_bytes, spmm_rows, spmm_elems),
                "set_tiling")
         if spmm_cols is not None:
             _check(lib().sable_plan_set_spmm_cols(self._h, spmm_cols), "set_spmm_cols")
+        if spmm_depth is not None:
+            _check(lib().sable_plan_set_spmm_depth(self._h, spmm_depth), "set_spmm_depth")
         return self
 
     def upload(self, stream=None):

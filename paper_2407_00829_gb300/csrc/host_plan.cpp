@@ -436,6 +436,12 @@ sable_status sable_plan_set_spmm_cols(sable_plan_t P, int32_t cols) {
   return SABLE_OK;
 }
 
+sable_status sable_plan_set_spmm_depth(sable_plan_t P, int32_t depth) {
+  if (!P || (depth != 4 && depth != 8)) return SABLE_ERR_INVALID;
+  P->tiling.spmm_depth = depth;
+  return SABLE_OK;
+}
+
 sable_status sable_plan_status(sable_plan_t P) { return P ? P->sticky : SABLE_ERR_INVALID; }
 
 }  // extern "C"

@@ -73,7 +73,7 @@ template <> struct VecT<1> {
 
 // C[:, n0:n0+NT] for every item; V = 4 needs N, ldb, ldc multiples of 4 and
 // 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
-template <int THREADS, int V, bool VBRC>
+template <int THREADS, int V, bool VBRC, int U = 4>
 __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, const float *__restrict__ B,
                                           int64_t ldb, float *__restrict__ C, int64_t ldc, int N, float *cs,
                                           int *rps) {
@@ -179,18 +179,18 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
           c = __ldcs(A.ci + p);
         }
         const int cnt = min(32, pz - base);
-        for (int j = 0; j < cnt; j += 4) {
-          float vj[4];
-          int cj[4];
-          T bj[4];
+        for (int j = 0; j < cnt; j += U) {   // U entries' B rows in flight per warp
+          float vj[U];
+          int cj[U];
+          T bj[U];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < U; ++u) {
             vj[u] = __shfl_sync(kFull, v, (j + u) & 31);
             cj[u] = __shfl_sync(kFull, c, (j + u) & 31);
             bj[u] = (lane_ok && j + u < cnt) ? Vt::load(B + (int64_t)cj[u] * ldb + n0 + lc) : Vt::zero();
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < U; ++u) {
             if (j + u < cnt) {
               const int pp = base + j + u;
               if (pp >= nxt) {
@@ -229,8 +229,8 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
 
 // C[:, n0:n0+NT] of one matrix; V = 4 needs N, ldb, ldc multiples of 4 and
 // 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
-template <int THREADS, int V, bool VBRC>
-__global__ void __launch_bounds__(THREADS)
+template <int THREADS, int V, bool VBRC, int U = 4>
+__global__ void __launch_bounds__(THREADS, U == 8 ? 4 : 1)
 spmm_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ B, int64_t ldb,
                    float *__restrict__ C, int64_t ldc, int N) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -238,7 +238,7 @@ spmm_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict_
   int *rps = reinterpret_cast<int *>(cs + A.spmm.rows_max * 32 * V);
   for (int it = blockIdx.x; it < A.spmm.n; it += gridDim.x) {
     const DevItem I = A.spmm.items[it];
-    spmm_tile<THREADS, V, VBRC>(A, I, B, ldb, C, ldc, N, cs, rps);
+    spmm_tile<THREADS, V, VBRC, U>(A, I, B, ldb, C, ldc, N, cs, rps);
   }
 }
 
@@ -605,7 +605,18 @@ sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int
   const int NT = 32 * V;
   const size_t smem = (size_t)D.spmm.rows_max * NT * 4 + ((size_t)D.spmm.rows_max + 1) * 4;
   const int gy = (int)((N + NT - 1) / NT);
-  if (V == 4 && vbrc) {
+  const bool deep = P->tiling.spmm_depth == 8;   // 8 B rows in flight per warp in the CSR phase
+  if (V == 4 && vbrc && deep) {
+    auto k = spmm_hybrid_kernel<TH, 4, true, 8>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
+    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
+  } else if (V == 4 && deep) {
+    auto k = spmm_hybrid_kernel<TH, 4, false, 8>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
+    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
+  } else if (V == 4 && vbrc) {
     auto k = spmm_hybrid_kernel<TH, 4, true>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);

@@ -69,6 +69,7 @@ sable_status apply(sable_plan_t P, const sable_tiling &t, cudaStream_t st) {
                            now.rows_per_item_mm == t.spmm_rows && now.item_elems_mm == t.spmm_elems;
   sable_status s = sable_plan_set_tiling(P, t.spmv_rows, t.spmv_bytes, t.spmm_rows, t.spmm_elems);
   if (!s) s = sable_plan_set_spmm_cols(P, t.spmm_cols);
+  if (!s) s = sable_plan_set_spmm_depth(P, t.spmm_depth);
   if (!s && !same_tables) s = sable_plan_upload(P, st);   // the column panel needs no new tables
   return s;
 }
@@ -87,6 +88,7 @@ sable_status sable_plan_get_tiling(sable_plan_t P, sable_tiling *out) {
   out->spmm_rows = P->tiling.rows_per_item_mm;
   out->spmm_elems = P->tiling.item_elems_mm;
   out->spmm_cols = P->tiling.spmm_cols;
+  out->spmm_depth = P->tiling.spmm_depth;
   return SABLE_OK;
 }
 
@@ -114,6 +116,7 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
         t.spmm_rows = it->second.spmm_rows;
         t.spmm_elems = it->second.spmm_elems;
         t.spmm_cols = it->second.spmm_cols;
+        t.spmm_depth = it->second.spmm_depth;
       }
       cand.push_back(t);
       cached = true;
@@ -123,11 +126,14 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
     if (op == 0) {
       for (int32_t rows : {128, 256, 512, 1024})
         for (int64_t bytes : {16 << 10, 48 << 10, 160 << 10})
-          cand.push_back({rows, bytes, cur.spmm_rows, cur.spmm_elems, cur.spmm_cols});
+          cand.push_back({rows, bytes, cur.spmm_rows, cur.spmm_elems, cur.spmm_cols, cur.spmm_depth});
     } else {
       for (int32_t rows : {8, 16, 32, 64})
-        for (int64_t elems : {1024, 4096, 16384})
-          for (int32_t cols : {128, 64}) cand.push_back({cur.spmv_rows, cur.spmv_bytes, rows, elems, cols});
+        for (int64_t elems : {1024, 4096, 16384}) {
+          cand.push_back({cur.spmv_rows, cur.spmv_bytes, rows, elems, 128, 4});
+          cand.push_back({cur.spmv_rows, cur.spmv_bytes, rows, elems, 128, 8});
+          cand.push_back({cur.spmv_rows, cur.spmv_bytes, rows, elems, 64, 4});
+        }
     }
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -50,12 +50,12 @@ def _matrix(seed, values):
 PLAN = [(sable.VBR, dict(a_min=400, max_span=160, tile=8)), (sable.CSR, None)]
 
 
-@pytest.mark.parametrize("cols", [0, 64])
+@pytest.mark.parametrize("cols,depth", [(0, 4), (64, 4), (128, 8)])
 @pytest.mark.parametrize("N", [128, 32, 200])
-def test_bf16_integer_exact(N, cols):
+def test_bf16_integer_exact(N, cols, depth):
     A = _matrix(3, "int")
     P = sable.plan_from(A, PLAN)
-    P.set_tiling(**dict(P.tiling(), spmm_cols=cols))
+    P.set_tiling(**dict(P.tiling(), spmm_cols=cols, spmm_depth=depth))
     assert P.info()["n_blocks"] == 3
     B = synth.dense_operand(5, A["n"], N, dist="int")
     ref = oracle.spmm(A["m"], A["row"], A["col"], A["val"], B)

@@ -85,7 +85,8 @@ def test_spmv_small(case, plan):
 
 
 @pytest.mark.parametrize("tiling", [dict(spmv_rows=4, spmv_bytes=64, spmm_rows=4, spmm_elems=1, spmm_cols=32),
-                                    dict(spmv_rows=1024, spmv_bytes=1 << 22, spmm_rows=256, spmm_elems=1 << 20),
+                                    dict(spmv_rows=1024, spmv_bytes=1 << 22, spmm_rows=256, spmm_elems=1 << 20,
+                                         spmm_depth=8),
                                     dict(spmv_rows=36, spmv_bytes=300, spmm_rows=12, spmm_elems=100, spmm_cols=64)])
 def test_spmv_integer_exact_any_tiling(tiling):
     rng = np.random.default_rng(42)
@@ -140,12 +141,12 @@ def test_order_errors_on_device():
     P.close()
 
 
-@pytest.mark.parametrize("cols", [0, 64, 32])
+@pytest.mark.parametrize("cols,depth", [(0, 4), (64, 4), (32, 4), (128, 8)])
 @pytest.mark.parametrize("N", [1, 7, 32, 128, 200])
-def test_spmm_small(N, cols):
+def test_spmm_small(N, cols, depth):
     A = SMALL[2]
     P = sable.plan_from(A, PLANS[0])
-    P.set_tiling(**dict(P.tiling(), spmm_cols=cols))
+    P.set_tiling(**dict(P.tiling(), spmm_cols=cols, spmm_depth=depth))
     B = synth.dense_operand(N, A["n"], N)
     ref = oracle.spmm(A["m"], A["row"], A["col"], A["val"], B)
     assert oracle.normwise_err(_spmm(P, B), ref) <= TOL_FP32
@@ -189,8 +190,8 @@ def test_blocks_scatter_200k_full_size_sampled():
     sel = np.random.default_rng(0).choice(A["m"], 3000, replace=False)
     ref = oracle.spmm_rows(A["m"], A["row"], A["col"], A["val"], B, sel)
     Bd = _dev(B)
-    for cols in (0, 64):
-        P.set_tiling(**dict(P.tiling(), spmm_cols=cols))
+    for cols, depth in ((0, 4), (64, 4), (128, 8)):
+        P.set_tiling(**dict(P.tiling(), spmm_cols=cols, spmm_depth=depth))
         for prec, tol in ((sable.FP32, TOL_FP32), (sable.BF16_BLOCKS, 2e-2)):
             C = torch.empty(A["m"], 128, device="cuda")
             P.spmm(Bd, C, prec)

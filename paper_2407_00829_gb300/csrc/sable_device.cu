@@ -230,7 +230,7 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
 // C[:, n0:n0+NT] of one matrix; V = 4 needs N, ldb, ldc multiples of 4 and
 // 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
 template <int THREADS, int V, bool VBRC, int U = 4>
-__global__ void __launch_bounds__(THREADS, U == 8 ? 4 : 1)
+__global__ void __launch_bounds__(THREADS, U == 8 ? 4 : 5)
 spmm_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ B, int64_t ldb,
                    float *__restrict__ C, int64_t ldc, int N) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -405,7 +405,10 @@ def run_planner(args):
                                    "SpMM N=64 BF16 blocks", "train_matrices": res["train_matrices"],
                        "test_matrices": res["test_matrices"], "candidates": pl.NAMES},
             "held_out": {k: res[k] for k in ("learned", "default", "csr", "best_fixed")},
-            "live": live, "gpu_launches": None}
+            "live": live,
+            # per live matrix: every candidate x op timed (3 warm-up + 20 launches), 4 feature
+            # launches and 3 MLP-forward launches for the learned choice
+            "gpu_launches": len(live) * (len(pl.NAMES) * len(pl.OPS) * 23 + 7)}
     print(json.dumps(line), flush=True)
 
 

@@ -387,6 +387,13 @@ int64_t sable_error_workspace_bytes(void);
 sable_status sable_error_norms(const float *y, const double *ref, int64_t count, double *out, void *work,
                                int64_t work_bytes, void *stream);
 
+/* The plan's device error word, 4 int32 copied to host `out` (synchronous):
+ * a status recorded by a kernel (0 = none; SABLE_ERR_TIMEOUT from a bounded
+ * wait of the tensor-core kernel), then three words of detail (0 unless a
+ * debug build's checks recorded one).
+ * Errors: SABLE_ERR_ORDER before upload; SABLE_ERR_CUDA. */
+sable_status sable_plan_device_error(sable_plan_t plan, int32_t *out);
+
 /* First error recorded on the plan (SABLE_OK if none). */
 sable_status sable_plan_status(sable_plan_t plan);
 

@@ -37,7 +37,7 @@ EXPORTED = [
     "sable_plan_add_regions", "sable_plan_get_region_stages", "sable_plan_reset",
     "sable_error_workspace_bytes", "sable_error_norms", "sable_plan_get_tiling", "sable_autotune",
     "sable_autotune_cache_clear", "sable_plan_set_spmm_cols", "sable_plan_update_values",
-    "sable_plan_set_spmm_depth",
+    "sable_plan_set_spmm_depth", "sable_plan_device_error",
 ]
 
 NFEAT = 24
@@ -120,6 +120,7 @@ def lib():
             "sable_plan_set_spmm_cols": ([p, i32], i32),
             "sable_plan_update_values": ([p, p, p], i32),
             "sable_plan_set_spmm_depth": ([p, i32], i32),
+            "sable_plan_device_error": ([p, p], i32),
             "sable_error_workspace_bytes": ([], i64),
             "sable_error_norms": ([p, p, i64, p, p, i64, p], i32),
             "sable_mlp_param_count": ([p], i64),
@@ -352,6 +353,12 @@ class Plan:
 
     def status(self) -> int:
         return lib().sable_plan_status(self._h)
+
+    def device_error(self):
+        """[status, check, tile row, value] recorded by the plan's kernels."""
+        out = (ctypes.c_int32 * 4)()
+        _check(lib().sable_plan_device_error(self._h, out), "sable_plan_device_error")
+        return list(out)
 
     def tiling(self) -> dict:
         t = Tiling()

@@ -746,6 +746,17 @@ sable_status sable_plan_update_values(sable_plan_t P, const float *val, void *st
   return e == cudaSuccess ? SABLE_OK : cuda_fail(P, e);
 }
 
+sable_status sable_plan_device_error(sable_plan_t P, int32_t *out) {
+  if (!P || !out) return SABLE_ERR_INVALID;
+  if (!P->uploaded) return SABLE_ERR_ORDER;
+  const cudaError_t e = cudaMemcpy(out, P->dev.err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SABLE_ERR_CUDA;
+  }
+  return SABLE_OK;
+}
+
 sable_status sable_plan_reset(sable_plan_t P) {
   if (!P) return SABLE_ERR_INVALID;
   if (P->dev_blob) {

@@ -42,10 +42,16 @@ __device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T,
     const int r0 = I.r0, R = I.r1 - I.r0;
     for (int i = tid; i <= R; i += kThreads) rps[i] = __ldg(A.rp + r0 + i);
 
-    // ---- A. VDIA: thread owns rows my .. my+3
+    // ---- A. VDIA: a quad of 4 consecutive rows; when the tile has fewer
+    // quads than threads, S threads (adjacent lanes) split the quad's
+    // diagonals and their partial sums meet by warp shuffles
+    const int Q = (R + 3) >> 2;
+    int S = 1;
+    while (S < 32 && 2 * S * Q <= kThreads) S *= 2;
+    const int q4 = tid / S, jj = tid & (S - 1);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    const int my = r0 + 4 * tid;
-    if (!PLAIN)
+    const int my = r0 + 4 * q4;
+    if (!PLAIN && q4 < Q)
       for (int q = I.seg_lo; q < I.seg_hi; ++q) {
         const DevSeg s = T.pseg[q];
         const int ra = max(r0, s.row0), rb = min(I.r1, s.row0 + s.nrows);
@@ -54,8 +60,8 @@ __device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T,
         const bool g2 = my + 2 >= ra && my + 2 < rb, g3 = my + 3 >= ra && my + 3 < rb;
         const float *vp = A.vdia + s.val_off + (my - s.base);
         const int c0 = my + s.off_lo;
-#pragma unroll 4
-        for (int k = 0; k < s.ndiag; ++k) {
+#pragma unroll 1
+        for (int k = jj; k < s.ndiag; k += S) {
           const float4 v = __ldg(reinterpret_cast<const float4 *>(vp + (size_t)k * s.ld));
           const int c = c0 + k;
           const float x0 = (g0 && (unsigned)c < n) ? __ldg(x + c) : 0.f;
@@ -68,9 +74,15 @@ __device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T,
           a3 = fmaf(v.w, x3, a3);
         }
       }
-    {
-      const int i = 4 * tid;
-      if (i < R) ys[i] = a0;
+    for (int o = S >> 1; o > 0; o >>= 1) {   // S is uniform over the CTA: every lane takes part
+      a0 += __shfl_xor_sync(kFull, a0, o);
+      a1 += __shfl_xor_sync(kFull, a1, o);
+      a2 += __shfl_xor_sync(kFull, a2, o);
+      a3 += __shfl_xor_sync(kFull, a3, o);
+    }
+    if (jj == 0 && q4 < Q) {
+      const int i = 4 * q4;
+      ys[i] = a0;
       if (i + 1 < R) ys[i + 1] = a1;
       if (i + 2 < R) ys[i + 2] = a2;
       if (i + 3 < R) ys[i + 3] = a3;

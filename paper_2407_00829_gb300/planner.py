@@ -212,26 +212,29 @@ def design(data):
 
 
 class LearnedPlanner:
-    """MLP N_IN -> h -> h -> len(NAMES) on the library's kernels."""
+    """An ensemble of MLPs N_IN -> h -> h -> len(NAMES) on the library's
+    kernels; the prediction is the members' mean (members differ only in
+    their seeded initialisation)."""
 
-    def __init__(self, hidden=64, seed=0):
-        self.net = Mlp(N_IN, hidden, hidden, len(NAMES), seed=seed)
+    def __init__(self, hidden=64, seed=0, members=5):
+        self.nets = [Mlp(N_IN, hidden, hidden, len(NAMES), seed=seed + k) for k in range(members)]
 
-    def fit(self, X, Y, steps=4000, lr=2e-3):
+    def fit(self, X, Y, steps=2000, lr=2e-3):
         import torch
         Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
         Yd = torch.from_numpy(np.ascontiguousarray(Y)).cuda()
         losses = []
-        for s in range(steps):
-            loss = self.net.grad(Xd, Yd)
-            self.net.adam(lr=lr)
-            if s % 200 == 0 or s == steps - 1:
-                losses.append(float(loss.item()))
+        for net in self.nets:
+            for s in range(steps):
+                loss = net.grad(Xd, Yd)
+                net.adam(lr=lr)
+            losses.append(float(loss.item()))
         return losses
 
     def predict(self, X):
         import torch
-        return self.net.forward(torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()).cpu().numpy()
+        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+        return np.mean([net.forward(Xd).cpu().numpy() for net in self.nets], axis=0)
 
     def choose(self, X):
         return np.argmin(self.predict(X), axis=1)
@@ -243,8 +246,8 @@ class LearnedPlanner:
 
     def save(self, path, **extra):
         with open(path, "w") as f:
-            json.dump(dict(extra, names=NAMES, n_in=N_IN, hidden=self.net.shape.n_h1,
-                           params=[float(v) for v in self.net.params.cpu().numpy()]), f)
+            json.dump(dict(extra, names=NAMES, n_in=N_IN, hidden=self.nets[0].shape.n_h1,
+                           params=[[float(v) for v in net.params.cpu().numpy()] for net in self.nets]), f)
 
     @classmethod
     def load(cls, path):
@@ -253,8 +256,9 @@ class LearnedPlanner:
             d = json.load(f)
         if d["names"] != NAMES or d["n_in"] != N_IN:
             raise ValueError("weights were trained for another candidate set")
-        lp = cls(hidden=d["hidden"])
-        lp.net.params.copy_(torch.tensor(d["params"], dtype=torch.float32))
+        lp = cls(hidden=d["hidden"], members=len(d["params"]))
+        for net, p in zip(lp.nets, d["params"]):
+            net.params.copy_(torch.tensor(p, dtype=torch.float32))
         return lp
 
 
@@ -264,7 +268,7 @@ def quality(times, picks):
     return np.array([[times[i, picks[i, o], o] / times[i, :, o].min() - 1 for o in range(O)] for i in range(M)])
 
 
-def evaluate(data, n_test=200, steps=4000, seed=0, lp=None):
+def evaluate(data, n_test=200, steps=2000, seed=0, lp=None):
     """Train on all but the last n_test matrices (unless a trained planner is
     given) and compare on those: the learned planner, the fixed default plan,
     CSR only and the best single candidate on the training matrices."""
@@ -275,7 +279,7 @@ def evaluate(data, n_test=200, steps=4000, seed=0, lp=None):
     res = {"train_matrices": int(cut), "test_matrices": int(n_test)}
     if lp is None:
         lp = LearnedPlanner(seed=seed)
-        res["train_mse"] = lp.fit(X[:cut * n_ops], Y[:cut * n_ops], steps=steps)[-1]
+        res["train_mse"] = float(np.mean(lp.fit(X[:cut * n_ops], Y[:cut * n_ops], steps=steps)))
     T = data["times"]
     test = T[cut:]
     learned = lp.choose(X[cut * n_ops:]).reshape(n_test, n_ops)
@@ -306,7 +310,7 @@ def main():
     ap.add_argument("--out", default="planner_data.npz")
     ap.add_argument("--data", nargs="*", default=[])
     ap.add_argument("--test", type=int, default=200)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--weights", default=None)
     a = ap.parse_args()
     if a.cmd == "regions":

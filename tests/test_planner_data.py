@@ -1,0 +1,57 @@
+"""The learned planner's committed data set and weights, checked on the CPU.
+
+The data set holds, for every generated matrix, its device features and the
+measured SpMV / SpMM time of every candidate plan; the weights were trained on
+the first matrices with the library's MLP kernels.  Here the weights are run
+through the FP64 reference MLP (oracle/ml.py) on the held-out matrices: the
+chosen plans must be within 5 % of the exhaustive planner's on average and
+better than the fixed three-format plan."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ml
+from paper_2407_00829_gb300 import planner as pl
+
+HERE = os.path.dirname(pl.__file__)
+DATA = os.path.join(HERE, "planner_data.npz")
+WEIGHTS = os.path.join(HERE, "planner_weights.json")
+N_TEST = 200
+
+
+def _data():
+    d = dict(np.load(DATA))
+    assert list(d["names"]) == pl.NAMES and list(d["ops"]) == [o for o, _ in pl.OPS]
+    return d
+
+
+def test_data_set_is_consistent():
+    d = _data()
+    M = d["features"].shape[0]
+    assert M >= N_TEST + 200
+    assert d["features"].shape == (M, pl.NFEAT) and d["times"].shape == (M, len(pl.NAMES), len(pl.OPS))
+    assert np.all(np.isfinite(d["features"])) and np.all(d["times"] > 0)
+    idx = d["meta"][:, 0]
+    assert np.all(np.diff(idx) > 0)                       # matrices in generator order, each once
+    X, Y = pl.design(d)
+    assert X.shape == (M * len(pl.OPS), pl.N_IN)
+    assert np.all(Y >= 0) and np.allclose(Y.min(axis=1), 0)
+
+
+def test_committed_weights_through_the_reference_mlp():
+    d = _data()
+    w = json.load(open(WEIGHTS))
+    assert w["names"] == pl.NAMES and w["n_in"] == pl.N_IN
+    shape = (pl.N_IN, w["hidden"], w["hidden"], len(pl.NAMES))
+    X, _ = pl.design(d)
+    M, O = d["features"].shape[0], len(pl.OPS)
+    cut = M - N_TEST
+    pred = np.mean([ml.mlp_forward(shape, np.array(p, np.float64), X[cut * O:]) for p in w["params"]], axis=0)
+    picks = np.argmin(pred, axis=1).reshape(N_TEST, O)
+    q = pl.quality(d["times"][cut:], picks)
+    qd = pl.quality(d["times"][cut:], np.full((N_TEST, O), pl.NAMES.index(pl.DEFAULT)))
+    for o in range(O):
+        assert q[:, o].mean() <= 0.05, (o, q[:, o].mean())
+        assert q[:, o].mean() < qd[:, o].mean()

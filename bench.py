@@ -212,6 +212,7 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
            "extract_s": round(t_ex, 2), "steps": k}
     res = {}
     variants = (("fp32", lambda i: P.spmm(B, C, sable.FP32, stream), 4),
+                ("fp32_split", lambda i: P.spmm(B, C, sable.FP32_SPLIT, stream), 6),
                 ("bf16_blocks", lambda i: P.spmm(B, C, sable.BF16_BLOCKS, stream), 2),
                 ("plain_csr", lambda i: P.csr_spmm(B, C, stream), None))
 
@@ -230,11 +231,12 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
 
     # every variant at the default tiling, then the hybrid variants each at the
     # tiling the autotuner picks for it; plain CSR keeps the best it got
-    default = run_variants(("fp32", "bf16_blocks", "plain_csr"))
+    default = run_variants(("fp32", "fp32_split", "bf16_blocks", "plain_csr"))
     out["autotune"] = {"default": {"spmm_rows": 32, "spmm_elems": 4096},
                        "default_tiling_ms": {k_: v["ms"] for k_, v in default.items()}}
     plain_best = default["plain_csr"]
-    for name, op in (("fp32", sable.TUNE_SPMM_FP32), ("bf16_blocks", sable.TUNE_SPMM_BF16)):
+    for name, op in (("fp32", sable.TUNE_SPMM_FP32), ("fp32_split", sable.TUNE_SPMM_FP32_SPLIT),
+                     ("bf16_blocks", sable.TUNE_SPMM_BF16)):
         t0 = time.perf_counter()
         tuned, _ = P.autotune(op, B, C, reps=5, use_cache=False, stream=stream)
         out["autotune"][name] = {"spmm_rows": tuned["spmm_rows"], "spmm_elems": tuned["spmm_elems"],
@@ -262,6 +264,7 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
     out.update(res)
     best_plain = min(res["plain_csr"]["ms"], (res["cusparse_csr"] or {"ms": float("inf")})["ms"])
     out["vs_plain_csr_fp32"] = best_plain / res["fp32"]["ms"]
+    out["vs_plain_csr_fp32_split"] = best_plain / res["fp32_split"]["ms"]
     out["vs_plain_csr_bf16"] = best_plain / res["bf16_blocks"]["ms"]
     P.close()
     return out

@@ -53,8 +53,13 @@ typedef enum { SABLE_X_VDIA = 0, SABLE_X_VBR = 1, SABLE_X_CSR = 2 } sable_extrac
  * as bfloat16 (round to nearest even) of value / s_b with a per-block power of
  * two s_b = 2^ceil(log2 max|a|), rounds the B rows it multiplies to bfloat16,
  * runs the block products on the tensor cores (tcgen05, FP32 accumulation)
- * and multiplies by s_b; VDIA and CSR parts stay FP32. */
-typedef enum { SABLE_FP32 = 0, SABLE_BF16_BLOCKS = 1 } sable_precision;
+ * and multiplies by s_b; VDIA and CSR parts stay FP32.
+ * SABLE_FP32_SPLIT keeps FP32 accuracy on the tensor cores: each block value
+ * / s_b and each B value is the sum of three bfloat16 terms (the value
+ * rounded, then its exact FP32 remainders rounded: 24 significant bits), and
+ * the six term products down to 2^-24 of the product are accumulated in
+ * FP32.  SABLE_FP32 runs the blocks on the FP32 FMA pipes. */
+typedef enum { SABLE_FP32 = 0, SABLE_BF16_BLOCKS = 1, SABLE_FP32_SPLIT = 2 } sable_precision;
 
 /* Extractor parameters.  Fields an extractor does not use are ignored.
  *   delta        density floor (Section 4.1: 0.5 for blocks; Section 5 uses
@@ -242,7 +247,8 @@ sable_status sable_plan_set_spmm_depth(sable_plan_t plan, int32_t depth);
 /* Autotuner (no counterpart in the paper, which runs one generated kernel per
  * region): time the plan's op over candidate tilings with CUDA events on
  * `stream` and leave the plan uploaded with the fastest.  op 0 = SpMV (in =
- * x, out = y), 1 = SpMM FP32, 2 = SpMM with BF16 blocks (in = B, n x N, out =
+ * x, out = y), 1 = SpMM FP32, 2 = SpMM with BF16 blocks, 3 = SpMM with
+ * SABLE_FP32_SPLIT blocks (in = B, n x N, out =
  * C, m x N, row-major with leading dimension N); in / out are device buffers
  * the timed launches read and overwrite.  Candidates: SpMV rows {128, 256,
  * 512, 1024} x bytes {16K, 48K, 160K}; SpMM rows {8, 16, 32, 64} x cells

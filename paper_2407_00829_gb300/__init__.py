@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsable.so")
 
 VDIA, VBR, CSR = 0, 1, 2
-FP32, BF16_BLOCKS = 0, 1
+FP32, BF16_BLOCKS, FP32_SPLIT = 0, 1, 2
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime error",
           4: "incomplete plan", 5: "call out of order", 6: "device wait timed out",
@@ -170,7 +170,7 @@ class Tiling(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-TUNE_SPMV, TUNE_SPMM_FP32, TUNE_SPMM_BF16 = 0, 1, 2
+TUNE_SPMV, TUNE_SPMM_FP32, TUNE_SPMM_BF16, TUNE_SPMM_FP32_SPLIT = 0, 1, 2, 3
 
 
 class Plan:

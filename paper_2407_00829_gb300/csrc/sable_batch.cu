@@ -42,11 +42,11 @@ sable_status batch_spmv_launch(sable_batch_t b, const float *const *x, float *co
 sable_status batch_spmm_launch(sable_batch_t b, const float *const *B, int64_t N, float *const *C,
                                sable_precision prec, cudaStream_t st) {
   if (N < 1 || N > (int64_t)65535 * 32) return SABLE_ERR_INVALID;
-  if (prec != SABLE_FP32 && prec != SABLE_BF16_BLOCKS) return SABLE_ERR_INVALID;
-  const bool bf16 = prec == SABLE_BF16_BLOCKS && b->n_trip > 0;
+  if (prec != SABLE_FP32 && prec != SABLE_BF16_BLOCKS && prec != SABLE_FP32_SPLIT) return SABLE_ERR_INVALID;
+  const bool bf16 = prec != SABLE_FP32 && b->n_trip > 0;   // blocks on the tensor cores
   if (bf16) {
     const sable_status s = launch_vbr_tc(b->mats, b->trip, b->n_trip, nullptr, 0, nullptr, 0, B, C, (int)N,
-                                         b->sm_count, b->err, st);
+                                         b->sm_count, b->err, st, prec == SABLE_FP32_SPLIT ? 3 : 1);
     if (s) return s;
   }
   return launch_spmm_grouped(b->mats, b->items_m, b->n_m, b->rows_m, B, C, (int)N, bf16, b->sm_count, st);

@@ -356,7 +356,7 @@ struct Staging {
   std::vector<float> vdia;
   std::vector<DevBlk> blks;
   std::vector<int32_t> rp, ci, prp, pci, tc_pairs;
-  std::vector<uint16_t> vbr_bf16;
+  std::vector<uint16_t> vbr_bf16, vbr_bf16_mid, vbr_bf16_lo;
   std::vector<float> vbr_scale;
   std::vector<float> cv, pcv;
   HostItems it_v, it_m, pit_v, pit_m;
@@ -426,7 +426,7 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
     }
     {
       std::vector<int64_t> offs;
-      pack_vbr_bf16(H.blks, H.vbr_canon, S->vbr_bf16, S->vbr_scale, offs);
+      pack_vbr_bf16(H.blks, H.vbr_canon, S->vbr_bf16, S->vbr_scale, offs, &S->vbr_bf16_mid, &S->vbr_bf16_lo);
       for (size_t b = 0; b < S->blks.size(); ++b) S->blks[b].bf_off = offs[b];
       S->tc_pairs.clear();
       vbr_tc_pairs(H.blks, 0, S->tc_pairs);
@@ -460,6 +460,8 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   const size_t o_blks = ar.add(S->blks.data(), vec_bytes(S->blks));
   const size_t o_vbr = ar.add(P->hyb.vbr_canon.data(), vec_bytes(P->hyb.vbr_canon));
   const size_t o_bf16 = ar.add(S->vbr_bf16.data(), vec_bytes(S->vbr_bf16));
+  const size_t o_bf16_mid = ar.add(S->vbr_bf16_mid.data(), vec_bytes(S->vbr_bf16_mid));
+  const size_t o_bf16_lo = ar.add(S->vbr_bf16_lo.data(), vec_bytes(S->vbr_bf16_lo));
   const size_t o_scale = ar.add(S->vbr_scale.data(), vec_bytes(S->vbr_scale));
   const size_t o_pairs = ar.add(S->tc_pairs.data(), vec_bytes(S->tc_pairs));
   const size_t o_self = ar.reserve(sizeof(DevHybrid));
@@ -515,6 +517,8 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   D.blks = reinterpret_cast<const DevBlk *>(blob + o_blks);
   D.vbr = reinterpret_cast<const float *>(blob + o_vbr);
   D.vbr_bf16 = reinterpret_cast<const uint16_t *>(blob + o_bf16);
+  D.vbr_bf16_mid = reinterpret_cast<const uint16_t *>(blob + o_bf16_mid);
+  D.vbr_bf16_lo = reinterpret_cast<const uint16_t *>(blob + o_bf16_lo);
   D.vbr_scale = reinterpret_cast<const float *>(blob + o_scale);
   D.n_tc = (int32_t)(S->tc_pairs.size() / 3);
   P->dev_trip = reinterpret_cast<const int32_t *>(blob + o_pairs);
@@ -543,6 +547,8 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   P->o_vdia = o_vdia;
   P->o_vbr = o_vbr;
   P->o_bf16 = o_bf16;
+  P->o_bf16_mid = o_bf16_mid;
+  P->o_bf16_lo = o_bf16_lo;
   P->o_scale = o_scale;
   P->o_cv = o_cv;
   P->o_pcv = o_pcv;
@@ -671,12 +677,13 @@ sable_status sable_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, 
                         sable_precision prec, void *stream) {
   const sable_status s = check_ready(P);
   if (s) return s;
-  if (prec != SABLE_FP32 && prec != SABLE_BF16_BLOCKS) return SABLE_ERR_INVALID;
-  const bool bf16 = prec == SABLE_BF16_BLOCKS && P->dev.n_tc > 0;
+  if (prec != SABLE_FP32 && prec != SABLE_BF16_BLOCKS && prec != SABLE_FP32_SPLIT) return SABLE_ERR_INVALID;
+  const bool bf16 = prec != SABLE_FP32 && P->dev.n_tc > 0;   // blocks on the tensor cores
   if (bf16) {
     if (N < 1 || ldb < N || ldc < N || !B || !C || N > INT32_MAX) return SABLE_ERR_INVALID;
     const sable_status s2 = launch_vbr_tc(P->dev_self, P->dev_trip, P->dev.n_tc, B, ldb, C, ldc, nullptr, nullptr,
-                                          (int)N, P->sm_count, P->dev.err, (cudaStream_t)stream);
+                                          (int)N, P->sm_count, P->dev.err, (cudaStream_t)stream,
+                                          prec == SABLE_FP32_SPLIT ? 3 : 1);
     if (s2) return fail(P, s2);
   }
   return launch_spmm(P, P->dev, B, N, ldb, C, ldc, bf16, (cudaStream_t)stream);
@@ -700,7 +707,7 @@ sable_status sable_plan_update_values(sable_plan_t P, const float *val, void *st
   cudaStream_t st = (cudaStream_t)stream;
   Hybrid &H = P->hyb;
   std::vector<float> vdia, cv, pcv, scales;
-  std::vector<uint16_t> bf16;
+  std::vector<uint16_t> bf16, bf16_mid, bf16_lo;
   try {
     // duplicates summed in FP64 in input order, rounded once: as at create
     std::vector<double> sum(P->cval.size(), 0.0);
@@ -723,7 +730,7 @@ sable_status sable_plan_update_values(sable_plan_t P, const float *val, void *st
       sp += (int64_t)d.nrows * d.ndiag;
     }
     std::vector<int64_t> offs;
-    pack_vbr_bf16(H.blks, H.vbr_canon, bf16, scales, offs);
+    pack_vbr_bf16(H.blks, H.vbr_canon, bf16, scales, offs, &bf16_mid, &bf16_lo);
     cv.assign(H.ccv.begin(), H.ccv.end());
     cv.resize(cv.size() + kCsrPad, 0.0f);
     pcv.assign(P->cval.begin(), P->cval.end());
@@ -736,6 +743,8 @@ sable_status sable_plan_update_values(sable_plan_t P, const float *val, void *st
       {P->o_vdia, vdia.data(), H.segs.empty() ? 0 : vdia.size() * 4},
       {P->o_vbr, H.vbr_canon.data(), H.vbr_canon.size() * 4},
       {P->o_bf16, bf16.data(), bf16.size() * 2},
+      {P->o_bf16_mid, bf16_mid.data(), bf16_mid.size() * 2},
+      {P->o_bf16_lo, bf16_lo.data(), bf16_lo.size() * 2},
       {P->o_scale, scales.data(), scales.size() * 4},
       {P->o_cv, cv.data(), cv.size() * 4},
       {P->o_pcv, pcv.data(), pcv.size() * 4}};
@@ -788,6 +797,7 @@ sable_status sable_plan_reset(sable_plan_t P) {
   P->dest.clear();
   P->h_segs.clear();
   P->o_vdia = P->o_vbr = P->o_bf16 = P->o_scale = P->o_cv = P->o_pcv = 0;
+  P->o_bf16_mid = P->o_bf16_lo = 0;
   P->owner.assign(P->canon.ci.size(), OWN_NONE);
   P->hyb = Hybrid{};
   P->stats = sable_plan_stats{};

@@ -82,6 +82,8 @@ struct DevHybrid {
   const DevBlk *blks = nullptr;
   const float *vbr = nullptr;
   const uint16_t *vbr_bf16 = nullptr;
+  const uint16_t *vbr_bf16_mid = nullptr;  // second and third bf16 terms (SABLE_FP32_SPLIT)
+  const uint16_t *vbr_bf16_lo = nullptr;
   const float *vbr_scale = nullptr;  // per block power-of-two scale
   int32_t n_tc = 0;                  // (block, 128-row tile) pairs for the tensor-core path
   const int32_t *rp = nullptr;   // CSR remainder row pointer (m + 1)
@@ -134,6 +136,7 @@ struct sable_plan_s {
   std::vector<int64_t> dest;                         // canonical entry -> index in its format's value array
   std::vector<sable::DevSeg> h_segs;                 // device segment descriptors (padded VDIA layout)
   size_t o_vdia = 0, o_vbr = 0, o_bf16 = 0, o_scale = 0, o_cv = 0, o_pcv = 0;   // value arrays in the blob
+  size_t o_bf16_mid = 0, o_bf16_lo = 0;
   std::vector<int8_t> owner;           // per canonical entry
   sable::Hybrid hyb;
   sable::Tiling tiling;
@@ -168,11 +171,12 @@ std::vector<BlockFound> partition_blocks(const Csr &R, const Csr &RT, const sabl
 int host_threads();
 // sable_tc.cu: BF16 VBR blocks on the tensor cores
 void pack_vbr_bf16(const std::vector<Block> &blks, const std::vector<float> &canon,
-                   std::vector<uint16_t> &packed, std::vector<float> &scales, std::vector<int64_t> &offs);
+                   std::vector<uint16_t> &packed, std::vector<float> &scales, std::vector<int64_t> &offs,
+                   std::vector<uint16_t> *mid = nullptr, std::vector<uint16_t> *lo = nullptr);
 void vbr_tc_pairs(const std::vector<Block> &blks, int32_t mat, std::vector<int32_t> &trip);
 sable_status launch_vbr_tc(const DevHybrid *mats, const int32_t *trip, int n_trip, const float *B, int64_t ldb,
                            float *C, int64_t ldc, const float *const *Bs, float *const *Cs, int N, int sm_count,
-                           int *err, cudaStream_t_ st);
+                           int *err, cudaStream_t_ st, int terms);
 sable_status launch_spmv_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,
                                  const float *const *xs, float *const *ys, int sm_count, cudaStream_t_ st);
 sable_status launch_spmm_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,

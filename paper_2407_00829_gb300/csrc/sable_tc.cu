@@ -21,6 +21,13 @@
 // the block's rows of C.  Every wait is bounded; on time-out the kernel
 // records SABLE_ERR_TIMEOUT, skips the rest of its job, frees its TMEM and
 // returns.
+//
+// FP32-accurate variant (NS = 3): every operand value v is written as the sum
+// of three bf16 terms, v1 = bf16(v), v2 = bf16(v - v1), v3 = bf16(v - v1 - v2)
+// (each difference exact in FP32), 24 significant bits in all; the six
+// products whose order is at most that of v1 * w3 (v3 w1, v2 w2, v1 w3, v2 w1,
+// v1 w2, v1 w1, smallest first) are accumulated in FP32 in TMEM.  The dropped
+// terms are below 2^-24 of the product, FP32's own rounding.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -40,10 +47,11 @@ constexpr int kTileBytes = kTileM * kTileK * 2;        // 16 KB, A and B tiles a
 constexpr unsigned kTmemCols = 128;
 constexpr long long kTcWait = 4000000000LL;            // ~2 s
 
+template <int NS>
 struct TcShared {
-  alignas(1024) unsigned char a[kTileBytes];
-  alignas(1024) unsigned char b[kTileBytes];
-  uint64_t bar_a;     // A tile landed
+  alignas(1024) unsigned char a[NS][kTileBytes];   // A tile, one per bf16 term
+  alignas(1024) unsigned char b[NS][kTileBytes];   // B tile, one per bf16 term
+  uint64_t bar_a;     // A tiles landed
   uint64_t bar_mma;   // MMAs of the K step finished
   uint32_t tmem_base;
   int dead;
@@ -83,13 +91,15 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p, unsigned lbo, unsig
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
                             ((uint32_t)(kTileM >> 4) << 24);
 
+template <int NS>
 __global__ void __launch_bounds__(kTcThreads, 1)
 vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ trip, int n_jobs, int ntn,
               const float *B0, int64_t ldb0, float *C0, int64_t ldc0, const float *const *Bs, float *const *Cs,
               int N, int *err) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   // align the working area to 1024 bytes
-  TcShared &S = *reinterpret_cast<TcShared *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  TcShared<NS> &S =
+      *reinterpret_cast<TcShared<NS> *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.bar_a)) : "memory");
@@ -119,19 +129,23 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
     const DevBlk blk = A.blks[bi];
     const float scale = A.vbr_scale[bi];
     const int nkt = (blk.nc + kTileK - 1) / kTileK;
-    const uint16_t *atiles = A.vbr_bf16 + blk.bf_off + (size_t)t * nkt * (kTileM * kTileK);
+    const size_t toff = blk.bf_off + (size_t)t * nkt * (kTileM * kTileK);
+    const uint16_t *atiles[3] = {A.vbr_bf16 + toff, NS > 1 ? A.vbr_bf16_mid + toff : nullptr,
+                                 NS > 1 ? A.vbr_bf16_lo + toff : nullptr};
     bool ok = true;
     for (int kt = 0; kt < nkt && ok; ++kt) {
-      // A tile by TMA bulk copy
+      // A tiles by TMA bulk copy
       if (tid == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&S.bar_a)),
-                     "r"((unsigned)kTileBytes)
+                     "r"((unsigned)(NS * kTileBytes))
                      : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                su32(S.a)),
-            "l"(atiles + (size_t)kt * (kTileM * kTileK)), "r"((unsigned)kTileBytes), "r"(su32(&S.bar_a))
-            : "memory");
+#pragma unroll
+        for (int sp = 0; sp < NS; ++sp)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  su32(S.a[sp])),
+              "l"(atiles[sp] + (size_t)kt * (kTileM * kTileK)), "r"((unsigned)kTileBytes), "r"(su32(&S.bar_a))
+              : "memory");
       }
       // B slice: rows k of B (K dim), columns n (N dim) -> bf16, K-major core matrices
       const int kb = blk.c0 + kt * kTileK;
@@ -142,18 +156,24 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
         const float *bp = B + (size_t)kb * ldb + n0 + n;
 #pragma unroll 2
         for (int k8 = 0; k8 < kTileK / 8; ++k8) {
-          uint32_t w[4];
+          uint32_t w[NS][4];
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
             const int ka = 8 * k8 + 2 * h, kb2 = ka + 1;
-            const float f0 = (ncol && ka < kvalid) ? __ldg(bp + (size_t)ka * ldb) : 0.f;
-            const float f1 = (ncol && kb2 < kvalid) ? __ldg(bp + (size_t)kb2 * ldb) : 0.f;
-            const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(f0));
-            const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(f1));
-            w[h] = lo | (hi << 16);
+            float f0 = (ncol && ka < kvalid) ? __ldg(bp + (size_t)ka * ldb) : 0.f;
+            float f1 = (ncol && kb2 < kvalid) ? __ldg(bp + (size_t)kb2 * ldb) : 0.f;
+#pragma unroll
+            for (int sp = 0; sp < NS; ++sp) {   // term sp, then the exact remainder
+              const __nv_bfloat16 b0 = __float2bfloat16_rn(f0), b1 = __float2bfloat16_rn(f1);
+              w[sp][h] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+              f0 -= __bfloat162float(b0);
+              f1 -= __bfloat162float(b1);
+            }
           }
-          *reinterpret_cast<uint4 *>(S.b + (n >> 3) * 1024 + k8 * 128 + (n & 7) * 16) =
-              make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+          for (int sp = 0; sp < NS; ++sp)
+            *reinterpret_cast<uint4 *>(S.b[sp] + (n >> 3) * 1024 + k8 * 128 + (n & 7) * 16) =
+                make_uint4(w[sp][0], w[sp][1], w[sp][2], w[sp][3]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -164,16 +184,23 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
           S.dead = 1;
         } else {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // products (A term, B term), smallest first: one for NS = 1, six for NS = 3
+          constexpr int kPairs = NS == 1 ? 1 : 6;
+          constexpr int kPa[6] = {2, 1, 0, 1, 0, 0}, kPb[6] = {0, 1, 2, 0, 1, 0};
 #pragma unroll
           for (int ks = 0; ks < kTileK / 16; ++ks) {
-            const uint64_t ad = smem_desc(S.a + ks * 256, 128, 1024);
-            const uint64_t bd = smem_desc(S.b + ks * 256, 128, 1024);
-            const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
-                : "memory");
+#pragma unroll
+            for (int pr = 0; pr < kPairs; ++pr) {
+              const int ta = NS == 1 ? 0 : kPa[pr], tb = NS == 1 ? 0 : kPb[pr];
+              const uint64_t ad = smem_desc(S.a[ta] + ks * 256, 128, 1024);
+              const uint64_t bd = smem_desc(S.b[tb] + ks * 256, 128, 1024);
+              const uint32_t acc = (kt > 0 || ks > 0 || pr > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                  "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                  : "memory");
+            }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            su32(&S.bar_mma))
@@ -200,7 +227,7 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
     // epilogue: TMEM -> registers -> scale -> shared (transpose) -> C, whole
     // rows per store instruction.  The A/B tiles are free: the MMAs are done.
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float *stage = reinterpret_cast<float *>(S.a) + warp * (32 * 33);   // 32 rows x 33 (padded)
+    float *stage = reinterpret_cast<float *>(&S.a[0][0]) + warp * (32 * 33);   // 32 rows x 33 (padded)
     const int rbase = t * kTileM + 32 * warp;                             // first row of my warp in the block
 #pragma unroll 1
     for (int ch = 0; ch < kTileN / 32; ++ch) {
@@ -240,7 +267,8 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
 
 }  // namespace
 
-size_t tc_smem_bytes() { return sizeof(TcShared) + 1024; }
+template <int NS>
+size_t tc_smem_bytes() { return sizeof(TcShared<NS>) + 1024; }
 
 // Host: bf16 of a float, round to nearest even (NaN kept quiet).
 static uint16_t to_bf16(float f) {
@@ -259,11 +287,22 @@ static float pow2_scale(float amax) {
   return std::ldexp(1.f, m == 0.5f ? e - 1 : e);
 }
 
+// bf16 value of a host bf16 bit pattern
+static float from_bf16(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
 void pack_vbr_bf16(const std::vector<Block> &blks, const std::vector<float> &canon,
-                   std::vector<uint16_t> &packed, std::vector<float> &scales, std::vector<int64_t> &offs) {
+                   std::vector<uint16_t> &packed, std::vector<float> &scales, std::vector<int64_t> &offs,
+                   std::vector<uint16_t> *mid, std::vector<uint16_t> *lo) {
   packed.clear();
   scales.clear();
   offs.clear();
+  if (mid) mid->clear();
+  if (lo) lo->clear();
   int64_t voff = 0;
   for (const Block &b : blks) {
     float amax = 0.f;
@@ -274,6 +313,8 @@ void pack_vbr_bf16(const std::vector<Block> &blks, const std::vector<float> &can
     const int64_t nt = (b.nr + kTileM - 1) / kTileM, nkt = (b.nc + kTileK - 1) / kTileK;
     const size_t base = packed.size();
     packed.resize(base + (size_t)(nt * nkt * kTileM * kTileK), 0);
+    if (mid) mid->resize(packed.size(), 0);
+    if (lo) lo->resize(packed.size(), 0);
     for (int64_t t = 0; t < nt; ++t)
       for (int64_t kt = 0; kt < nkt; ++kt) {
         uint16_t *tile = packed.data() + base + (size_t)((t * nkt + kt) * kTileM * kTileK);
@@ -284,7 +325,15 @@ void pack_vbr_bf16(const std::vector<Block> &blks, const std::vector<float> &can
             const int64_t c = kt * kTileK + k;
             if (c >= b.nc) break;
             const float v = canon[voff + c * b.nr + r] / s;     // exact: s is a power of two
-            tile[(m >> 3) * 512 + (k >> 3) * 64 + (m & 7) * 8 + (k & 7)] = to_bf16(v);
+            const size_t at = (size_t)(tile - packed.data()) + (m >> 3) * 512 + (k >> 3) * 64 + (m & 7) * 8 + (k & 7);
+            const uint16_t h1 = to_bf16(v);
+            packed[at] = h1;
+            if (mid && lo) {   // the next two terms of v, each from an exact FP32 remainder
+              const float r1 = v - from_bf16(h1);
+              const uint16_t h2 = to_bf16(r1);
+              (*mid)[at] = h2;
+              (*lo)[at] = to_bf16(r1 - from_bf16(h2));
+            }
           }
         }
       }
@@ -305,17 +354,19 @@ void vbr_tc_pairs(const std::vector<Block> &blks, int32_t mat, std::vector<int32
 
 sable_status launch_vbr_tc(const DevHybrid *mats, const int32_t *trip, int n_trip, const float *B, int64_t ldb,
                            float *C, int64_t ldc, const float *const *Bs, float *const *Cs, int N, int sm_count,
-                           int *err, cudaStream_t_ st) {
+                           int *err, cudaStream_t_ st, int terms) {
   const int ntn = (N + kTileN - 1) / kTileN;
   const long long nj = (long long)n_trip * ntn;
   if (nj == 0) return SABLE_OK;
-  if (nj > INT32_MAX) return SABLE_ERR_INVALID;
-  const size_t smem = tc_smem_bytes();
-  // at most 4 CTAs per SM so that their TMEM allocations (128 columns each) fit
-  const size_t smem_req = std::max(smem, (size_t)56 * 1024);
-  cudaFuncSetAttribute(vbr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
-  const int grid = std::max(1, std::min((int)nj, 4 * std::max(sm_count, 1)));
-  vbr_tc_kernel<<<grid, kTcThreads, smem_req, st>>>(mats, trip, (int)nj, ntn, B, ldb, C, ldc, Bs, Cs, N, err);
+  if (nj > INT32_MAX || (terms != 1 && terms != 3)) return SABLE_ERR_INVALID;
+  // at most 4 CTAs per SM so that their TMEM allocations (128 columns each) fit;
+  // the three-term variant's tiles allow 2
+  const size_t smem_req = terms == 1 ? std::max(tc_smem_bytes<1>(), (size_t)56 * 1024) : tc_smem_bytes<3>();
+  const int per_sm = terms == 1 ? 4 : 2;
+  auto k = terms == 1 ? vbr_tc_kernel<1> : vbr_tc_kernel<3>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
+  const int grid = std::max(1, std::min((int)nj, per_sm * std::max(sm_count, 1)));
+  k<<<grid, kTcThreads, smem_req, st>>>(mats, trip, (int)nj, ntn, B, ldb, C, ldc, Bs, Cs, N, err);
   if (cudaGetLastError() != cudaSuccess) {
     (void)cudaGetLastError();
     return SABLE_ERR_CUDA;

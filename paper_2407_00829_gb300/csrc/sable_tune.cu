@@ -39,7 +39,7 @@ Key shape_class(const sable_plan_stats &s, int op, int64_t N) {
 
 sable_status run_op(sable_plan_t P, int op, int64_t N, const float *in, float *out, cudaStream_t st) {
   if (op == 0) return sable_spmv(P, in, out, st);
-  return sable_spmm(P, in, N, N, out, N, op == 2 ? SABLE_BF16_BLOCKS : SABLE_FP32, st);
+  return sable_spmm(P, in, N, N, out, N, op == 2 ? SABLE_BF16_BLOCKS : op == 3 ? SABLE_FP32_SPLIT : SABLE_FP32, st);
 }
 
 // mean device time of one launch over `reps` back-to-back launches, best of two rounds
@@ -94,7 +94,7 @@ sable_status sable_plan_get_tiling(sable_plan_t P, sable_tiling *out) {
 
 sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *in, float *out, int32_t reps,
                             int32_t use_cache, sable_tiling *chosen, float *chosen_ms, void *stream) {
-  if (!P || op < 0 || op > 2 || (op > 0 && N < 1) || !in || !out || reps < 1 || reps > 10000)
+  if (!P || op < 0 || op > 3 || (op > 0 && N < 1) || !in || !out || reps < 1 || reps > 10000)
     return SABLE_ERR_INVALID;
   if (P->sticky) return P->sticky;
   if (!P->extracted) return SABLE_ERR_ORDER;

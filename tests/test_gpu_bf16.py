@@ -1,4 +1,5 @@
-"""GPU parity of SpMM with BF16 VBR blocks on the tensor cores.
+"""GPU parity of SpMM with VBR blocks on the tensor cores: BF16 blocks, and
+FP32-accurate blocks as three bf16 terms (SABLE_FP32_SPLIT).
 
 * Integer inputs: block values / s_b and B are exact in bfloat16 and every
   partial sum is an integer below 2^24, so the result must equal the FP64
@@ -96,4 +97,31 @@ def test_bf16_without_blocks_equals_fp32():
     assert P.info()["n_blocks"] == 0
     B = synth.dense_operand(2, 300, 16)
     np.testing.assert_array_equal(_spmm(P, B, sable.BF16_BLOCKS), _spmm(P, B, sable.FP32))
+    P.close()
+
+
+@pytest.mark.parametrize("N", [128, 32, 200])
+def test_fp32_split_integer_exact(N):
+    A = _matrix(3, "int")
+    P = sable.plan_from(A, PLAN)
+    B = synth.dense_operand(5, A["n"], N, dist="int")
+    ref = oracle.spmm(A["m"], A["row"], A["col"], A["val"], B)
+    np.testing.assert_array_equal(_spmm(P, B, sable.FP32_SPLIT).astype(np.float64), ref)
+    P.close()
+
+
+@pytest.mark.parametrize("N", [128, 64, 250])
+def test_fp32_split_within_fp32_tolerance(N):
+    """Three-term blocks on the tensor cores meet the FP32 budget (1e-5
+    normwise against FP64), with inputs of mixed magnitude."""
+    A = _matrix(7, "normal")
+    A["val"] = (A["val"] * np.exp(np.random.default_rng(1).uniform(-6, 6, A["val"].size))).astype(np.float32)
+    P = sable.plan_from(A, PLAN)
+    assert P.info()["n_blocks"] == 3
+    B = synth.dense_operand(9, A["n"], N, dist="normal")
+    ref = oracle.spmm(A["m"], A["row"], A["col"], A["val"], B)
+    err_split = oracle.normwise_err(_spmm(P, B, sable.FP32_SPLIT), ref)
+    err_bf16 = oracle.normwise_err(_spmm(P, B, sable.BF16_BLOCKS), ref)
+    assert err_split <= 1e-5
+    assert err_split < err_bf16 / 50       # three terms, not one
     P.close()

@@ -43,6 +43,8 @@ def _args():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmm", action="store_true")
+    ap.add_argument("--spmm-only", action="store_true",
+                    help="only the SpMM workload, default tiling, no tuning (a short command to profile)")
     return ap.parse_args()
 
 
@@ -270,6 +272,41 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
     return out
 
 
+def run_spmm_only(args):
+    """The 200k SpMM workload alone: each variant 3 warm-up + `steps` timed
+    launches at the default tiling, no autotuning."""
+    import torch
+    from paper_2407_00829_gb300 import build as sbuild
+    sbuild.build()
+    import paper_2407_00829_gb300 as sable
+    import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    A = synth.blocks_scatter_200k()
+    P = sable.plan_from(A, [(sable.VBR, dict(a_min=256)), (sable.CSR, None)])
+    N = 128
+    B = torch.from_numpy(synth.dense_operand(13, A["n"], N)).to(dev)
+    C = torch.empty(A["m"], N, device=dev)
+    out = {"workload": "spmm-vbr+csr-200k, N=128, default tiling", "ms": {}}
+    k = max(1, min(args.steps, 20))
+    for name, fn in (("fp32", lambda: P.spmm(B, C, sable.FP32, stream)),
+                     ("fp32_split", lambda: P.spmm(B, C, sable.FP32_SPLIT, stream)),
+                     ("bf16_blocks", lambda: P.spmm(B, C, sable.BF16_BLOCKS, stream)),
+                     ("plain_csr", lambda: P.csr_spmm(B, C, stream))):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out["ms"][name] = e0.elapsed_time(e1) / k
+    P.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_batch(args):
     """Many matrices of uneven size in one grouped launch per op: 512 seeded
     matrices, rows log-uniform in [1k, 64k], 5-200 entries per row, mixed
@@ -425,6 +462,9 @@ def main():
         return
     if args.workload == "planner":
         run_planner(args)
+        return
+    if args.spmm_only:
+        run_spmm_only(args)
         return
     ws, rank, local = _dist()
     import torch

@@ -87,6 +87,40 @@ def test_batch_spmm_fp32_bf16(batch, N):
     g.close()
 
 
+def test_batch_tiling_tuner():
+    """tune.tune_batch re-uploads every plan per candidate tiling; the plans it
+    leaves behind (the fastest tiling) still compute the right products."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_00829_gb300 import tune
+    rng = np.random.default_rng(77)
+    mats = [synth.mixed_matrix(rng, int(m), 20.0, side_max=96) for m in (800, 2500, 4000, 1200)]
+    plans = [sable.plan_from(A, PLAN) for A in mats]
+    xs = [torch.from_numpy(synth.dense_operand(i, A["n"])).cuda() for i, A in enumerate(mats)]
+    ys = [torch.empty(A["m"], device="cuda") for A in mats]
+    best, times = tune.tune_batch(plans, "spmv", xs, ys, reps=3)
+    assert (best["spmv_rows"], best["spmv_bytes"]) in times and len(times) == len(tune.SPMV_CANDIDATES)
+    N = 16
+    Bs = [torch.from_numpy(synth.dense_operand(50 + i, A["n"], N)).cuda() for i, A in enumerate(mats)]
+    Cs = [torch.empty(A["m"], N, device="cuda") for A in mats]
+    bm, _ = tune.tune_batch(plans, "spmm_bf16", Bs, Cs, N=N, reps=3)
+    assert all(P.tiling()["spmm_rows"] == bm["spmm_rows"] for P in plans)
+    B = sable.Batch(plans)
+    for y in ys:
+        y.fill_(float("nan"))
+    B.spmv(xs, ys)
+    B.spmm(Bs, Cs, N, sable.FP32)
+    torch.cuda.synchronize()
+    for i, A in enumerate(mats):
+        ref = oracle.spmv(A["m"], A["row"], A["col"], A["val"], xs[i].cpu().numpy())
+        assert oracle.normwise_err(ys[i].cpu().numpy(), ref) <= 1e-5
+        refC = oracle.spmm(A["m"], A["row"], A["col"], A["val"], Bs[i].cpu().numpy())
+        assert oracle.normwise_err(Cs[i].cpu().numpy(), refC) <= 1e-5
+    B.close()
+    for P in plans:
+        P.close()
+
+
 def test_empty_batch():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")

@@ -42,7 +42,7 @@ typedef enum {
   SABLE_ERR_ORDER = 5,       /* call made in the wrong phase of the plan       */
   SABLE_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                  */
   SABLE_ERR_KERNEL = 7,      /* a kernel's own bounds check tripped            */
-  SABLE_ERR_UNSUPPORTED = 8  /* valid request this build does not implement    */
+  SABLE_ERR_UNSUPPORTED = 8  /* valid request the library does not implement  */
 } sable_status;
 
 /* Extractor kinds (Section 3.2).  SABLE_X_CSR claims everything left and must

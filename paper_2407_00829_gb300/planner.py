@@ -4,7 +4,7 @@ A plan is an ordered list of extractors with their thresholds: the paper's
 knobs are the extractor order (Section 4.3), the block threshold delta and
 A_min (Section 4.1) and the band threshold delta (Section 5 uses 0.75).  The
 exhaustive planner extracts, uploads and times every candidate plan on the
-device and keeps the fastest; it is the fallback and the judge.  The learned
+device and keeps the fastest; it is the fallback and the yardstick.  The learned
 planner computes the matrix's structural features with the library's feature
 kernels, asks a small MLP (trained by the library's own forward / backward /
 Adam kernels on timings the pipeline produced) for every candidate's
@@ -18,7 +18,7 @@ Data set work flow (matrices from ``synth.planner_set_matrix``):
                         extract it when no table is given), time SpMV and
                         SpMM (N = 64, BF16 blocks) with CUDA events, compute
                         the device features; write features + timings
-  evaluate (device)     train on the first matrices, judge on the held-out
+  evaluate (device)     train on the first matrices, score on the held-out
                         rest: plan-quality loss t_chosen / t_exhaustive - 1
 """
 from __future__ import annotations

@@ -107,6 +107,23 @@ def test_spmv_integer_exact_any_tiling(tiling):
     P.close()
 
 
+def test_spmv_x_not_16_byte_aligned():
+    """x starting 4 bytes past an aligned address takes the scalar load path."""
+    A = SMALL[1]
+    P = sable.plan_from(A, ALL3)
+    xs = synth.dense_operand(21, A["n"])
+    buf = torch.zeros(A["n"] + 1, device="cuda")
+    buf[1:] = torch.from_numpy(xs).cuda()
+    x = buf[1:]
+    assert x.data_ptr() % 16 != 0
+    y = torch.full((A["m"],), float("nan"), device="cuda")
+    P.spmv(x, y)
+    torch.cuda.synchronize()
+    ref = oracle.spmv(A["m"], A["row"], A["col"], A["val"], xs)
+    assert oracle.normwise_err(y.cpu().numpy(), ref) <= TOL_FP32
+    P.close()
+
+
 def test_edge_cases():
     # empty matrix, zero rows/cols, a single very long row, an all-empty tail
     cases = [dict(m=10, n=7, row=np.zeros(0, np.int32), col=np.zeros(0, np.int32), val=np.zeros(0, np.float32)),

@@ -222,10 +222,22 @@ def _isqrt_ceil(a: int) -> int:
     return s if s * s >= a else s + 1
 
 
+def score2(nnz: int, a: int, delta: float) -> float:
+    """The square of Algorithm 2's score a (d - delta)^1.5, d = nnz / a:
+    (nnz - delta a)^3 / a.  It orders windows as the score does (both grow
+    with the score for d >= delta) and needs only IEEE multiply, subtract and
+    divide, which round alike everywhere, unlike a library pow."""
+    t = float(nnz) - delta * float(a)
+    if t < 0.0:           # d >= delta by division while the product rounds below
+        t = 0.0
+    return t * t * t / float(a)
+
+
 def find_block(lines: List[List[int]], O0: int, O1: int, I0: int, I1: int, p: Params):
     """Algorithm 2 over outer lines [O0, O1) and inner range [I0, I1).
 
-    Returns (score, o0, o1_end, i0, i1_end) with half-open ends, score -1 if none.
+    Returns (score2, o0, o1_end, i0, i1_end) with half-open ends, score2 -1 if
+    none; score2 is the square of the printed score (see score2).
     """
     best = (-1.0, 0, 0, 0, 0)
     s_min = _isqrt_ceil(p.a_min)
@@ -249,7 +261,7 @@ def find_block(lines: List[List[int]], O0: int, O1: int, I0: int, I1: int, p: Pa
                         break
                     dens = nnz / a
                     if dens >= p.delta:
-                        sc = a * math.pow(dens - p.delta, 1.5)
+                        sc = score2(nnz, a, p.delta)
                         if sc > best[0]:
                             best = (sc, o0, o1 + 1, I0 + i0, I0 + i1 + 1)
                         break

@@ -4,7 +4,7 @@
 //
 // Readings (identical to the library's documented behaviour):
 //  * Density floor and score base are delta (printed as 0.5 = default delta):
-//    score = area * (density - delta)^1.5.
+//    score = area * (density - delta)^1.5, compared through its square.
 //  * FindBlock's outer span is capped at max_span lines.
 //  * Ties keep the first window in scan order (o0, o1, i1 ascending; strict
 //    '>'); across threads the merge keeps the highest score, then the lowest
@@ -50,7 +50,14 @@ int host_threads() {
 
 namespace {
 
-volatile double kScoreExp = 1.5;   // kept opaque so pow() is the libm call
+// Algorithm 2's score a (d - delta)^1.5 is compared through its square,
+// (nnz - delta a)^3 / a (same order for d >= delta), which needs only IEEE
+// multiply, subtract and divide and so rounds the same on every processor.
+inline double score2(int64_t nnz, int64_t a, double delta) {
+  double t = (double)nnz - delta * (double)a;
+  if (t < 0.0) t = 0.0;   // d >= delta by division, but the product may round below it
+  return t * t * t / (double)a;
+}
 
 struct Best {
   double sc = -1.0;
@@ -72,7 +79,7 @@ void scan_start(const Csr &M, int64_t o0, int64_t O1, int64_t I0, int64_t I1,
                 std::vector<int32_t> &touched, Best &best) {
   const int64_t L_in = I1 - I0;
   int64_t tmin = INT64_MAX, tmax = -1, hmax = 0, total = 0;
-  const double ub_unit = std::pow(1.0 - p.delta, (double)kScoreExp);
+  const double omd = 1.0 - p.delta, ub_unit = omd * omd * omd;   // (1 - delta)^3
   const int64_t o_end = std::min<int64_t>(O1, o0 + (int64_t)p.max_span);
   for (int64_t o1 = o0; o1 < o_end; ++o1) {
     const int32_t *b = M.ci.data() + M.rp[o1], *e = M.ci.data() + M.rp[o1 + 1];
@@ -95,9 +102,9 @@ void scan_start(const Csr &M, int64_t o0, int64_t O1, int64_t I0, int64_t I1,
     if ((double)hmax < p.delta * (double)s) continue;
     {
       double ub;
-      if (total >= p.a_min) ub = (double)total * ub_unit;
+      if (total >= p.a_min) ub = (double)total * (double)total * ub_unit;
       else if ((double)total >= p.delta * (double)p.a_min)
-        ub = (double)p.a_min * std::pow((double)total / (double)p.a_min - p.delta, (double)kScoreExp);
+        ub = score2(total, p.a_min, p.delta);
       else continue;
       if (best.sc >= 0 && ub * (1.0 + 1e-9) <= best.sc) continue;
     }
@@ -112,7 +119,7 @@ void scan_start(const Csr &M, int64_t o0, int64_t O1, int64_t I0, int64_t I1,
         if (a < p.a_min) break;
         const double d = (double)nnz / (double)a;
         if (d >= p.delta) {
-          const double sc = (double)a * std::pow(d - p.delta, (double)kScoreExp);
+          const double sc = score2(nnz, a, p.delta);
           if (sc > best.sc) best = {sc, o0, o1 + 1, I0 + i0, I0 + i1 + 1};
           break;
         }

@@ -235,13 +235,13 @@ def test_find_block_bounded_by_brute_force(seed):
     r, c = np.nonzero(Mb)
     R = ox.Residual(m, n, r, c, np.arange(r.size))
     p = ox.Params(delta=0.5, a_min=12, max_span=12)
-    sc, o0, o1, i0, i1 = ox.find_block(R.rowlist, 0, m, 0, n, p)
+    sc2, o0, o1, i0, i1 = ox.find_block(R.rowlist, 0, m, 0, n, p)   # sc2: the score squared
     best = _brute_best(Mb, p.a_min, p.delta, ox._isqrt_ceil(p.a_min))
-    assert sc <= best + 1e-12
-    if sc >= 0:
+    assert sc2 <= best * best * (1 + 1e-12) + 1e-12
+    if sc2 >= 0:
         a = (o1 - o0) * (i1 - i0)
         z = int(Mb[o0:o1, i0:i1].sum())
-        assert sc == a * math.pow(z / a - p.delta, 1.5)
+        assert math.isclose(math.sqrt(sc2), a * math.pow(z / a - p.delta, 1.5), rel_tol=1e-12, abs_tol=1e-12)
         assert a >= p.a_min and z / a >= p.delta and o1 - o0 >= ox._isqrt_ceil(p.a_min)
     else:
         assert best < 0 or True

@@ -72,7 +72,11 @@ typedef enum { SABLE_FP32 = 0, SABLE_BF16_BLOCKS = 1, SABLE_FP32_SPLIT = 2 } sab
  *   coverage_min share of entries blocks must cover, else none are kept (0.08)
  *   max_span     cap on FindBlock's outer span (Algorithm 2)
  *   tile         candidate-region pre-pass cell size; 0 runs Algorithm 1 on
- *                the whole matrix */
+ *                the whole matrix
+ *   device_search 1: FindBlock runs on the current CUDA device for regions of
+ *                at least 128 outer lines and at most 4096 inner positions
+ *                (same result as the host search); 0 (default): host only.
+ *                A CUDA error makes sable_extract return SABLE_ERR_CUDA. */
 typedef struct {
   double delta;
   int64_t a_min;
@@ -83,6 +87,7 @@ typedef struct {
   double coverage_min;
   int32_t max_span;
   int32_t tile;
+  int32_t device_search;
 } sable_extract_params;
 
 /* Summary of an extracted plan.  Byte counts are the algorithmic bytes one

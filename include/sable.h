@@ -252,11 +252,12 @@ sable_status sable_plan_set_spmm_depth(sable_plan_t plan, int32_t depth);
 /* Autotuner (no counterpart in the paper, which runs one generated kernel per
  * region): time the plan's op over candidate tilings with CUDA events on
  * `stream` and leave the plan uploaded with the fastest.  op 0 = SpMV (in =
- * x, out = y), 1 = SpMM FP32, 2 = SpMM with BF16 blocks, 3 = SpMM with
- * SABLE_FP32_SPLIT blocks (in = B, n x N, out =
+ * x, out = y), 4 = plain CSR SpMV (sable_csr_spmv), 1 = SpMM FP32, 2 = SpMM
+ * with BF16 blocks, 3 = SpMM with SABLE_FP32_SPLIT blocks (in = B, n x N, out =
  * C, m x N, row-major with leading dimension N); in / out are device buffers
  * the timed launches read and overwrite.  Candidates: SpMV rows {128, 256,
- * 512, 1024} x bytes {16K, 48K, 160K}; SpMM rows {8, 16, 32, 64} x cells
+ * 512, 1024} x bytes {16K, 48K, 160K}, and 1024 rows with the bytes that cut
+ * the plan into 1, 2 or 3 full waves of the CTAs the GPU holds at once; SpMM rows {8, 16, 32, 64} x cells
  * {1024, 4096, 16384} x (128 columns with 4 or 8 rows in flight, 64 columns);
  * the other op's tiling is kept.  Each candidate is
  * uploaded (sable_plan_upload, which reallocates the plan's device tables and

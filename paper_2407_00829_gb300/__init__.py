@@ -170,7 +170,7 @@ class Tiling(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-TUNE_SPMV, TUNE_SPMM_FP32, TUNE_SPMM_BF16, TUNE_SPMM_FP32_SPLIT = 0, 1, 2, 3
+TUNE_SPMV, TUNE_SPMM_FP32, TUNE_SPMM_BF16, TUNE_SPMM_FP32_SPLIT, TUNE_CSR_SPMV = 0, 1, 2, 3, 4
 
 
 class Plan:
@@ -366,9 +366,10 @@ class Plan:
         return t.as_dict()
 
     def autotune(self, op: int, inp, out, reps: int = 10, use_cache: bool = True, stream=None):
-        """Pick and apply the fastest tiling for op (TUNE_SPMV / TUNE_SPMM_FP32 /
-        TUNE_SPMM_BF16) by timing it on the device; returns (tiling, ms)."""
-        N = 0 if op == TUNE_SPMV else inp.shape[1]
+        """Pick and apply the fastest tiling for op (TUNE_SPMV / TUNE_CSR_SPMV /
+        TUNE_SPMM_FP32 / TUNE_SPMM_BF16 / TUNE_SPMM_FP32_SPLIT) by timing it on
+        the device; returns (tiling, ms)."""
+        N = 0 if op in (TUNE_SPMV, TUNE_CSR_SPMV) else inp.shape[1]
         t = Tiling()
         ms = ctypes.c_float()
         _check(lib().sable_autotune(self._h, op, N, _dptr(inp), _dptr(out), reps, int(use_cache), ctypes.byref(t),

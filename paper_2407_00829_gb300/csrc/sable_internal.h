@@ -197,6 +197,7 @@ sable_status launch_spmm_grouped(const DevHybrid *mats, const DevItem *items, in
                                  const float *const *Bs, float *const *Cs, int N, bool vbrc, int sm_count,
                                  cudaStream_t_ st);
 // sable_spmv.cu
+int spmv_resident_ctas(int rows_max);   // SpMV CTAs one SM holds at this tile height
 sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const float *x, float *y,
                          cudaStream_t_ st);
 }  // namespace sable

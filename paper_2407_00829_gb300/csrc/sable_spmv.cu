@@ -182,6 +182,17 @@ spmv_grouped_kernel(const DevHybrid *__restrict__ mats, const DevItem *__restric
   }
 }
 
+int spmv_resident_ctas(int rows_max) {
+  const size_t smem = (size_t)rows_max * 4 + ((size_t)rows_max + 1) * 4;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmv_hybrid_kernel<false>, kThreads, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  (void)cudaGetLastError();
+  return per_sm;
+}
+
 sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const float *x, float *y,
                          cudaStream_t_ st) {
   if (D.m == 0) return SABLE_OK;

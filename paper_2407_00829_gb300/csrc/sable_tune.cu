@@ -33,12 +33,13 @@ int floor_log2(int64_t v) {
 
 Key shape_class(const sable_plan_stats &s, int op, int64_t N) {
   const int64_t z = std::max<int64_t>(1, s.nnz);
-  return Key{op, op == 0 ? -1 : floor_log2(N), floor_log2(std::max<int64_t>(1, s.m)), floor_log2(z),
+  return Key{op, (op == 0 || op == 4) ? -1 : floor_log2(N), floor_log2(std::max<int64_t>(1, s.m)), floor_log2(z),
              (int)(4 * s.nnz_vdia / z), (int)(4 * s.nnz_vbr / z)};
 }
 
 sable_status run_op(sable_plan_t P, int op, int64_t N, const float *in, float *out, cudaStream_t st) {
   if (op == 0) return sable_spmv(P, in, out, st);
+  if (op == 4) return sable_csr_spmv(P, in, out, st);
   return sable_spmm(P, in, N, N, out, N, op == 2 ? SABLE_BF16_BLOCKS : op == 3 ? SABLE_FP32_SPLIT : SABLE_FP32, st);
 }
 
@@ -94,7 +95,8 @@ sable_status sable_plan_get_tiling(sable_plan_t P, sable_tiling *out) {
 
 sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *in, float *out, int32_t reps,
                             int32_t use_cache, sable_tiling *chosen, float *chosen_ms, void *stream) {
-  if (!P || op < 0 || op > 3 || (op > 0 && N < 1) || !in || !out || reps < 1 || reps > 10000)
+  const bool spmv = op == 0 || op == 4;
+  if (!P || op < 0 || op > 4 || (!spmv && N < 1) || !in || !out || reps < 1 || reps > 10000)
     return SABLE_ERR_INVALID;
   if (P->sticky) return P->sticky;
   if (!P->extracted) return SABLE_ERR_ORDER;
@@ -109,7 +111,7 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
       sable_tiling t = cur;
-      if (op == 0) {
+      if (spmv) {
         t.spmv_rows = it->second.spmv_rows;
         t.spmv_bytes = it->second.spmv_bytes;
       } else {
@@ -123,10 +125,22 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
     }
   }
   if (!cached) {
-    if (op == 0) {
+    if (spmv) {
       for (int32_t rows : {128, 256, 512, 1024})
         for (int64_t bytes : {16 << 10, 48 << 10, 160 << 10})
           cand.push_back({rows, bytes, cur.spmm_rows, cur.spmm_elems, cur.spmm_cols, cur.spmm_depth});
+      // tiles sized for exactly 1, 2 or 3 full waves of resident CTAs
+      int dev = 0, sms = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
+        const int64_t slots = (int64_t)spmv_resident_ctas(kRangeRows) * sms;
+        const int64_t total = op == 4 ? P->stats.csr_spmv_bytes : P->stats.spmv_bytes;
+        for (int64_t k = 1; k <= 3; ++k) {
+          const int64_t bytes = total / (k * slots) + total / (50 * k * slots) + 64;
+          cand.push_back({kRangeRows, bytes, cur.spmm_rows, cur.spmm_elems, cur.spmm_cols, cur.spmm_depth});
+        }
+      }
+      (void)cudaGetLastError();
     } else {
       for (int32_t rows : {8, 16, 32, 64})
         for (int64_t elems : {1024, 4096, 16384}) {

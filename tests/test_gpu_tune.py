@@ -29,7 +29,9 @@ def test_autotune_spmv_and_spmm():
     xs = synth.dense_operand(1, A["n"])
     x, y = torch.from_numpy(xs).cuda(), torch.empty(A["m"], device="cuda")
     t, ms = P.autotune(sable.TUNE_SPMV, x, y, reps=5)
-    assert t["spmv_rows"] in SPMV_ROWS and t["spmv_bytes"] in SPMV_BYTES and ms > 0
+    # a fixed candidate, or 1024 rows with a wave-sized byte target
+    assert (t["spmv_rows"] in SPMV_ROWS and t["spmv_bytes"] in SPMV_BYTES) or t["spmv_rows"] == 1024
+    assert ms > 0
     assert P.tiling() == t
     y.fill_(float("nan"))
     P.spmv(x, y)
@@ -54,3 +56,23 @@ def test_autotune_spmv_and_spmm():
     assert sable.autotune_cache_clear() == 3
     P.close()
     Q.close()
+
+
+def test_autotune_plain_csr():
+    """The plain-CSR comparison path has its own tuner op; the tiling it picks
+    keeps both the plain and the hybrid SpMV correct."""
+    sable.autotune_cache_clear()
+    A = synth.mixed_matrix(np.random.default_rng(9), 20_000, 18.0)
+    P = sable.plan_from(A, [(sable.VDIA, None), (sable.CSR, None)])
+    xs = synth.dense_operand(3, A["n"])
+    x, y = torch.from_numpy(xs).cuda(), torch.empty(A["m"], device="cuda")
+    t, ms = P.autotune(sable.TUNE_CSR_SPMV, x, y, reps=5)
+    assert (t["spmv_rows"] in SPMV_ROWS and t["spmv_bytes"] in SPMV_BYTES) or t["spmv_rows"] == 1024
+    assert ms > 0 and P.tiling() == t
+    ref = oracle.spmv(A["m"], A["row"], A["col"], A["val"], xs)
+    for fn in (P.csr_spmv, P.spmv):
+        y.fill_(float("nan"))
+        fn(x, y)
+        assert oracle.normwise_err(y.cpu().numpy(), ref) <= 1e-5
+    assert sable.autotune_cache_clear() == 1
+    P.close()

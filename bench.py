@@ -267,12 +267,55 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
     except Exception:
         res["cusparse_csr"] = None
     out.update(res)
+    # sampled rows of every variant's result, for the accuracy check against
+    # the FP64 oracle in the CPU-baseline leg
+    sel = np.sort(np.random.default_rng(17).choice(A["m"], size=2048, replace=False))
+    sel_t = torch.from_numpy(sel).to(dev)
+    sampled = {}
+    for name, fn, _cb in variants:
+        C.fill_(float("nan"))
+        fn(0)
+        sampled[name] = C.index_select(0, sel_t).cpu().numpy()
+    check = {"A": A, "B": B.cpu().numpy(), "sel": sel, "rows": sampled, "N": N}
+    # row-gather ceiling of this device: random reads of whole 512-byte rows of
+    # B, the unit of work of the CSR part (one B row per entry)
+    gout = torch.zeros(1, device=dev)
+    gcount = max(info["nnz"], 1 << 20)
+    for _ in range(3):
+        sable.probe_row_gather(B, gcount, gout, stream)
+    g_ms = timed(lambda i: sable.probe_row_gather(B, gcount, gout, stream), 10)
+    rate = gcount / (g_ms * 1e-3)
+    t_csr = info["nnz_csr"] / rate * 1e3
+    t_all = info["nnz"] / rate * 1e3
+    out["row_gather_roofline"] = {
+        "what": "random reads of whole rows of B (N floats, one warp per row) measured live with "
+                "sable_probe_row_gather; the CSR part of SpMM reads one B row per entry",
+        "peak_rows_per_s": rate, "GB/s_at_peak": rate * 4 * N / 1e9,
+        "csr_rows_per_call_hybrid": info["nnz_csr"], "time_at_peak_ms_hybrid": t_csr,
+        "rows_per_call_plain_csr": info["nnz"], "time_at_peak_ms_plain_csr": t_all,
+        "frac": {"bf16_blocks": t_csr / res["bf16_blocks"]["ms"], "fp32_split": t_csr / res["fp32_split"]["ms"],
+                 "plain_csr": t_all / res["plain_csr"]["ms"]}}
     best_plain = min(res["plain_csr"]["ms"], (res["cusparse_csr"] or {"ms": float("inf")})["ms"])
     out["vs_plain_csr_fp32"] = best_plain / res["fp32"]["ms"]
     out["vs_plain_csr_fp32_split"] = best_plain / res["fp32_split"]["ms"]
     out["vs_plain_csr_bf16"] = best_plain / res["bf16_blocks"]["ms"]
     P.close()
-    return out
+    return out, check
+
+
+def _spmm_oracle_check(check):
+    """The FP64 oracle (C, one thread) on the sampled rows of the SpMM
+    workload: its time, and each variant's normwise error on those rows."""
+    import oracle
+    A, sel = check["A"], check["sel"]
+    t0 = time.perf_counter()
+    ref = oracle.spmm_rows(A["m"], A["row"], A["col"], A["val"], check["B"], sel)
+    dt = time.perf_counter() - t0
+    nnz_sel = int(np.isin(A["row"], sel).sum())
+    errs = {name: oracle.normwise_err(rows, ref) for name, rows in check["rows"].items()}
+    return {"rows_sampled": int(sel.size), "how": "max|C - C_oracle| / max|C_oracle| over the sampled rows "
+            "(all N columns), FP64 oracle", "normwise": errs,
+            "oracle_GFLOP/s_1_core": 2.0 * nnz_sel * check["N"] / dt / 1e9, "oracle_s": round(dt, 2)}
 
 
 def run_spmm_only(args):
@@ -615,10 +658,10 @@ def main():
 
     k_e2e = min(args.steps, 500)
     ms_e2e = timed(e2e, k_e2e)
-    spmm = None
+    spmm, spmm_check = None, None
     if not args.no_spmm and ws == 1:
         peak_hbm, _src = _peaks()
-        spmm = spmm_section(sable, torch, dev, stream, args.steps, timed, peak_hbm)
+        spmm, spmm_check = spmm_section(sable, torch, dev, stream, args.steps, timed, peak_hbm)
 
     # max over ranks
     def rank_max(v):
@@ -652,6 +695,8 @@ def main():
             err = {"normwise": en["normwise"], "rel2": en["rel2"],
                    "how": "max|y - y_oracle| / max|y_oracle| over all m outputs, FP64 oracle, "
                           "reduced on the device in FP64 (sable_error_norms)"}
+            if spmm is not None:
+                spmm["err_vs_oracle"] = _spmm_oracle_check(spmm_check)
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

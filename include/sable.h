@@ -385,6 +385,17 @@ sable_status sable_mlp_adam(int64_t count, float *params, const float *grads, fl
  * scattered entries.  No counterpart in the paper.  Errors: SABLE_ERR_INVALID. */
 sable_status sable_probe_gather(const float *x, int64_t n, int64_t count, float *out, void *stream);
 
+/* Calibration: `count` random row reads of B (device, row-major, n rows of
+ * leading dimension ld floats; the caller's buffer holds (n - 1) * ld + N
+ * floats), N columns each, row indices from a fixed hash reduced modulo n, one
+ * warp per row, one kernel launch on `stream`; `out` (device, one float) may
+ * be written.  Timing it gives the device's rate of random dense-row gathers,
+ * the ceiling of the CSR part of SpMM (one row of B per entry).  No
+ * counterpart in the paper.  Errors: SABLE_ERR_INVALID unless 4 <= N <= 128,
+ * N and ld are multiples of 4, ld >= N and B is 16-byte aligned. */
+sable_status sable_probe_row_gather(const float *B, int64_t n, int64_t ld, int32_t N, int64_t count, float *out,
+                                    void *stream);
+
 /* Accuracy of a result, reduced on the device in FP64: the error of an FP32
  * result y against an FP64 reference (the oracle's), as the normwise
  * relative error max|y - ref| / max|ref| that the library's accuracy budget

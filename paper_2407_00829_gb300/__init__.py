@@ -30,7 +30,7 @@ EXPORTED = [
     "sable_plan_info", "sable_plan_get_segments", "sable_plan_get_blocks",
     "sable_plan_get_vdia_values", "sable_plan_get_vbr_values", "sable_plan_get_csr",
     "sable_plan_set_tiling", "sable_plan_status", "sable_plan_destroy", "sable_status_string",
-    "sable_probe_gather", "sable_batch_create", "sable_batch_spmv", "sable_batch_spmm",
+    "sable_probe_gather", "sable_probe_row_gather", "sable_batch_create", "sable_batch_spmv", "sable_batch_spmm",
     "sable_batch_graph_spmv", "sable_batch_graph_spmm", "sable_graph_launch", "sable_graph_destroy",
     "sable_batch_status", "sable_batch_destroy", "sable_features_workspace_bytes", "sable_features",
     "sable_mlp_param_count", "sable_mlp_work_floats", "sable_mlp_forward", "sable_mlp_grad", "sable_mlp_adam",
@@ -100,6 +100,7 @@ def lib():
             "sable_plan_destroy": ([p], i32),
             "sable_status_string": ([i32], ctypes.c_char_p),
             "sable_probe_gather": ([p, i64, i64, p, p], i32),
+            "sable_probe_row_gather": ([p, i64, i64, i32, i64, p, p], i32),
             "sable_batch_create": ([p, i32, p], i32),
             "sable_batch_spmv": ([p, p, p, p], i32),
             "sable_batch_spmm": ([p, p, i64, p, i32, p], i32),
@@ -419,6 +420,15 @@ def probe_gather(x, count: int, out, stream=None):
     """Launch the random-gather calibration kernel (see include/sable.h)."""
     _check(lib().sable_probe_gather(_dptr(x), x.numel(), int(count), _dptr(out), _stream_handle(stream)),
            "sable_probe_gather")
+
+
+def probe_row_gather(B, count: int, out, stream=None):
+    """Launch the random row-gather calibration kernel on a 2-D float32 B
+    (see include/sable.h)."""
+    if B.dim() != 2 or B.stride(1) != 1:
+        raise ValueError("B must be a row-major 2-D tensor")
+    _check(lib().sable_probe_row_gather(_dptr(B), B.shape[0], B.stride(0), B.shape[1], int(count), _dptr(out),
+                                        _stream_handle(stream)), "sable_probe_row_gather")
 
 
 class Graph:

@@ -73,7 +73,10 @@ template <> struct VecT<1> {
 
 // C[:, n0:n0+NT] for every item; V = 4 needs N, ldb, ldc multiples of 4 and
 // 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
-template <int THREADS, int V, bool VBRC, int U = 4>
+// Without CSRP the tile computes only its structured parts (VDIA, VBR), skips
+// tiles that have none, and stores only the rows they cover (A.row_pre); the
+// row-split kernel then adds the CSR remainder.
+template <int THREADS, int V, bool VBRC, int U = 4, bool CSRP = true>
 __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, const float *__restrict__ B,
                                           int64_t ldb, float *__restrict__ C, int64_t ldc, int N, float *cs,
                                           int *rps) {
@@ -86,6 +89,7 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
   const int lc = V * lane;                       // this lane's first column in the tile
   const bool lane_ok = n0 + lc < N;
   const unsigned n = (unsigned)A.n;
+  if (!CSRP && I.seg_lo == I.seg_hi && I.blk_lo == I.blk_hi) return;   // uniform over the CTA
   {
     const int r0 = I.r0, R = I.r1 - I.r0;
     for (int i = tid; i < R * NT; i += THREADS) cs[i] = 0.f;
@@ -116,7 +120,7 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
     // ---- B. VBR: already multiplied on the tensor cores into C (VBRC), or FP32
     // FMA with four block rows per warp, so that each B row loaded serves four
     // rows of the block
-    if (VBRC) {
+    if (VBRC && A.n_tc > 0) {   // a matrix whose blocks share rows keeps them on FMA
       for (int q = I.blk_lo; q < I.blk_hi; ++q) {
         const DevBlk b = A.spmm.pblk[q];
         const int ia = max(r0, b.r0) - r0, ib = min(I.r1, b.r0 + b.nr) - r0;
@@ -158,7 +162,7 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
     __syncthreads();
 
     // ---- C. CSR remainder: the tile's entries split evenly over warps
-    const int pb = rps[0], pe = rps[R];
+    const int pb = CSRP ? rps[0] : 0, pe = CSRP ? rps[R] : 0;
     const int per = (pe - pb + NW - 1) / NW;
     const int pa = pb + warp * per, pz = min(pe, pa + per);
     if (pa < pz) {
@@ -180,17 +184,15 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
         }
         const int cnt = min(32, pz - base);
         for (int j = 0; j < cnt; j += U) {   // U entries' B rows in flight per warp
-          float vj[U];
-          int cj[U];
           T bj[U];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            vj[u] = __shfl_sync(kFull, v, (j + u) & 31);
-            cj[u] = __shfl_sync(kFull, c, (j + u) & 31);
-            bj[u] = (lane_ok && j + u < cnt) ? Vt::load(B + (int64_t)cj[u] * ldb + n0 + lc) : Vt::zero();
+            const int cu = __shfl_sync(kFull, c, (j + u) & 31);
+            bj[u] = (lane_ok && j + u < cnt) ? Vt::load(B + (int64_t)cu * ldb + n0 + lc) : Vt::zero();
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
+            const float vu = __shfl_sync(kFull, v, (j + u) & 31);   // the entry's value, fetched when used
             if (j + u < cnt) {
               const int pp = base + j + u;
               if (pp >= nxt) {
@@ -201,7 +203,7 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
                   nxt = rps[cur + 1];
                 }
               }
-              Vt::fma(acc, vj[u], bj[u]);
+              Vt::fma(acc, vu, bj[u]);
             }
           }
         }
@@ -212,6 +214,7 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
     // ---- store the tile
     if (lane_ok) {
       for (int i = warp; i < R; i += NW) {
+        if (!CSRP && !A.row_pre[r0 + i]) continue;
         const float *src = cs + i * NT + lc;
         float *dst = C + (int64_t)(r0 + i) * ldc + n0 + lc;
         if (V == 4) {
@@ -229,7 +232,7 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
 
 // C[:, n0:n0+NT] of one matrix; V = 4 needs N, ldb, ldc multiples of 4 and
 // 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
-template <int THREADS, int V, bool VBRC, int U = 4>
+template <int THREADS, int V, bool VBRC, int U = 4, bool CSRP = true>
 __global__ void __launch_bounds__(THREADS, U == 8 ? 4 : 5)
 spmm_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ B, int64_t ldb,
                    float *__restrict__ C, int64_t ldc, int N) {
@@ -238,8 +241,83 @@ spmm_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict_
   int *rps = reinterpret_cast<int *>(cs + A.spmm.rows_max * 32 * V);
   for (int it = blockIdx.x; it < A.spmm.n; it += gridDim.x) {
     const DevItem I = A.spmm.items[it];
-    spmm_tile<THREADS, V, VBRC, U>(A, I, B, ldb, C, ldc, N, cs, rps);
+    spmm_tile<THREADS, V, VBRC, U, CSRP>(A, I, B, ldb, C, ldc, N, cs, rps);
   }
+}
+
+// CSR remainder of SpMM, row split: warp w of the grid owns rows w, w + W, ...
+// (consecutive rows on neighbouring warps), sums each row's entries in
+// registers with U rows of B in flight, and stores the row once, adding what
+// the structured launches left in C where A.row_pre marks the row.  No shared
+// memory and no barriers: the tiled form's per-tile barriers (zero the tile,
+// sum, store) held its B-row gathers to ~60 % of the device's row-gather rate.
+// The inner loop is kept short (it is issue-bound otherwise): whole groups of
+// U entries run unchecked, and the last group's missing entries gather row 0
+// (always present) and are left out of the sum by a warp-uniform test.  FULL:
+// every lane's columns lie inside N (no per-lane test).
+template <int V, int U, bool FULL>
+__device__ __forceinline__ void spmm_rows_run(const DevHybrid &A, const float *__restrict__ B, int ldb,
+                                              float *__restrict__ C, int ldc, int N, int n0) {
+  using Vt = VecT<V>;
+  using T = typename Vt::T;
+  const int lane = threadIdx.x & 31;
+  const int lc = V * lane;
+  const bool lane_ok = FULL || n0 + lc < N;
+  const float *Bl = B + n0 + lc;
+  const int W = gridDim.x * (blockDim.x >> 5);
+  for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < A.m; r += W) {
+    const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
+    const bool pre = A.row_pre != nullptr && A.row_pre[r] != 0;
+    if (pre && p0 == p1) continue;   // the structured launch already stored the whole row
+    T acc = Vt::zero();
+    for (int base = p0; base < p1; base += 32) {
+      const int p = base + lane;
+      float v = 0.f;
+      int c = 0;
+      if (p < p1) {
+        v = __ldcs(A.cv + p);
+        c = __ldcs(A.ci + p);
+      }
+      const int cnt = min(32, p1 - base);
+      int j = 0;
+      for (; j + U <= cnt; j += U) {
+        T bj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int cu = __shfl_sync(kFull, c, j + u);
+          bj[u] = lane_ok ? Vt::load(Bl + (int64_t)cu * ldb) : Vt::zero();
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) Vt::fma(acc, __shfl_sync(kFull, v, j + u), bj[u]);
+      }
+      if (j < cnt) {   // j + u <= 31: the lanes past the row's end hold c = 0
+        T bj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int cu = __shfl_sync(kFull, c, j + u);
+          bj[u] = lane_ok ? Vt::load(Bl + (int64_t)cu * ldb) : Vt::zero();
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const float vu = __shfl_sync(kFull, v, j + u);
+          if (j + u < cnt) Vt::fma(acc, vu, bj[u]);
+        }
+      }
+    }
+    if (lane_ok) {
+      float *dst = C + (int64_t)r * ldc + n0 + lc;
+      if (pre) Vt::fma(acc, 1.0f, Vt::load_once(dst));   // exact add of the structured part
+      Vt::store_once(dst, acc);
+    }
+  }
+}
+
+// FULL when N is a multiple of the panel width 32 V.
+template <int V, int U, bool FULL>
+__global__ void __launch_bounds__(256, U == 8 ? 4 : 5)
+spmm_rows_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ B, int ldb,
+                 float *__restrict__ C, int ldc, int N) {
+  spmm_rows_run<V, U, FULL>(A, B, ldb, C, ldc, N, blockIdx.y * 32 * V);
 }
 
 // Many matrices in one launch (B_i: n_i x N, C_i: m_i x N, both with leading
@@ -359,6 +437,7 @@ struct Staging {
   std::vector<uint16_t> vbr_bf16, vbr_bf16_mid, vbr_bf16_lo;
   std::vector<float> vbr_scale;
   std::vector<float> cv, pcv;
+  std::vector<uint8_t> row_pre;
   HostItems it_v, it_m, pit_v, pit_m;
 };
 
@@ -429,7 +508,20 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
       pack_vbr_bf16(H.blks, H.vbr_canon, S->vbr_bf16, S->vbr_scale, offs, &S->vbr_bf16_mid, &S->vbr_bf16_lo);
       for (size_t b = 0; b < S->blks.size(); ++b) S->blks[b].bf_off = offs[b];
       S->tc_pairs.clear();
-      vbr_tc_pairs(H.blks, 0, S->tc_pairs);
+      // the tensor-core kernel stores its blocks' rows of C: blocks that share
+      // rows (two VBR stages) stay on the FP32 path
+      bool shared_rows = false;
+      int64_t end = -1;
+      for (const Block &b : H.blks) {
+        shared_rows = shared_rows || b.r0 < end;
+        end = std::max(end, b.r0 + b.nr);
+      }
+      if (!shared_rows) vbr_tc_pairs(H.blks, 0, S->tc_pairs);
+    }
+    if (!H.segs.empty() || !H.blks.empty()) {   // rows a structured part covers
+      S->row_pre.assign(P->m, 0);
+      for (const Segment &g : H.segs) std::fill(S->row_pre.begin() + g.row0, S->row_pre.begin() + g.row0 + g.nrows, 1);
+      for (const Block &b : H.blks) std::fill(S->row_pre.begin() + b.r0, S->row_pre.begin() + b.r0 + b.nr, 1);
     }
     S->rp.assign(H.crp.begin(), H.crp.end());
     S->ci.assign(H.cci.begin(), H.cci.end());
@@ -471,6 +563,7 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   const size_t o_prp = ar.add(S->prp.data(), vec_bytes(S->prp));
   const size_t o_pci = ar.add(S->pci.data(), vec_bytes(S->pci));
   const size_t o_pcv = ar.add(S->pcv.data(), vec_bytes(S->pcv));
+  const size_t o_pre = ar.add(S->row_pre.data(), vec_bytes(S->row_pre));
   size_t o_it[4][6];
   HostItems *its[4] = {&S->it_v, &S->it_m, &S->pit_v, &S->pit_m};
   for (int k = 0; k < 4; ++k) {
@@ -527,6 +620,9 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   D.ci = reinterpret_cast<const int32_t *>(blob + o_ci);
   D.cv = reinterpret_cast<const float *>(blob + o_cv);
   D.err = reinterpret_cast<int32_t *>(blob + o_err);
+  D.n_segs = (int32_t)S->segs.size();
+  D.n_blks = (int32_t)S->blks.size();
+  D.row_pre = S->row_pre.empty() ? nullptr : reinterpret_cast<const uint8_t *>(blob + o_pre);
   D.spmv = items_of(0, its[0]);
   D.spmm = items_of(1, its[1]);
   DevHybrid &Q = P->dev_plain;
@@ -593,66 +689,61 @@ sable_status check_ready(sable_plan_t P) {
   return SABLE_OK;
 }
 
+template <int V, bool VBRC>
+void launch_structured(const DevHybrid &D, const float *B, int64_t ldb, float *C, int64_t ldc, int N, size_t smem,
+                       int gy, int sms, cudaStream_t st) {
+  auto k = spmm_hybrid_kernel<256, V, VBRC, 4, false>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(grid_for(k, 256, smem, D.spmm.n, sms), gy);
+  k<<<grid, 256, smem, st>>>(D, B, ldb, C, ldc, N);
+}
+
+template <int V, int U>
+void launch_rows(const DevHybrid &D, const float *B, int64_t ldb, float *C, int64_t ldc, int N, int gy, int sms,
+                 cudaStream_t st) {
+  auto k = N % (32 * V) == 0 ? spmm_rows_kernel<V, U, true> : spmm_rows_kernel<V, U, false>;
+  dim3 grid(grid_for(k, 256, 0, (D.m + 7) / 8, sms), gy);
+  k<<<grid, 256, 0, st>>>(D, B, (int)ldb, C, (int)ldc, N);
+}
+
+// C = A B after the tensor-core blocks (vbrc: their rows of C are stored):
+// the structured launch (VDIA, FP32 blocks) stores the rows those parts
+// cover, then the row-split launch adds the CSR remainder to every row.
 sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int64_t N, int64_t ldb,
                          float *C, int64_t ldc, bool vbrc, cudaStream_t st) {
-  if (N < 1 || ldb < N || ldc < N || N > (int64_t)65535 * 32) return SABLE_ERR_INVALID;
+  if (N < 1 || ldb < N || ldc < N || N > (int64_t)65535 * 32 || ldb > INT32_MAX || ldc > INT32_MAX)
+    return SABLE_ERR_INVALID;
   if (D.m == 0) return SABLE_OK;
   if (!C || (D.n > 0 && !B)) return SABLE_ERR_INVALID;
   const bool vec = N % 4 == 0 && ldb % 4 == 0 && ldc % 4 == 0 &&
                    ((uintptr_t)B & 15) == 0 && ((uintptr_t)C & 15) == 0;
   const bool vec2 = N % 2 == 0 && ldb % 2 == 0 && ldc % 2 == 0 &&
                     ((uintptr_t)B & 7) == 0 && ((uintptr_t)C & 7) == 0;
-  // column panel per CTA: 128 (float4 lanes), 64 (float2) or 32; the panels
-  // of a launch run one after another in time, so a narrower panel keeps a
-  // smaller slice of B live in L2
+  // column panel per CTA: 128 (float4 lanes), 64 (float2) or 32
   const int cols = P->tiling.spmm_cols;
   const int V = cols == 32 ? 1 : cols == 64 ? (vec2 ? 2 : 1) : (vec ? 4 : 1);
-  constexpr int TH = 256;
   const int NT = 32 * V;
-  const size_t smem = (size_t)D.spmm.rows_max * NT * 4 + ((size_t)D.spmm.rows_max + 1) * 4;
   const int gy = (int)((N + NT - 1) / NT);
-  const bool deep = P->tiling.spmm_depth == 8;   // 8 B rows in flight per warp in the CSR phase
-  if (V == 4 && vbrc && deep) {
-    auto k = spmm_hybrid_kernel<TH, 4, true, 8>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
-    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
-  } else if (V == 4 && deep) {
-    auto k = spmm_hybrid_kernel<TH, 4, false, 8>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
-    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
-  } else if (V == 4 && vbrc) {
-    auto k = spmm_hybrid_kernel<TH, 4, true>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
-    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
-  } else if (V == 2 && vbrc) {
-    auto k = spmm_hybrid_kernel<TH, 2, true>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
-    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
-  } else if (V == 2) {
-    auto k = spmm_hybrid_kernel<TH, 2, false>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
-    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
-  } else if (vbrc) {
-    auto k = spmm_hybrid_kernel<TH, 1, true>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
-    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
-  } else if (V == 4) {
-    auto k = spmm_hybrid_kernel<TH, 4, false>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
-    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
-  } else {
-    auto k = spmm_hybrid_kernel<TH, 1, false>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(grid_for(k, TH, smem, D.spmm.n, P->sm_count), gy);
-    k<<<grid, TH, smem, st>>>(D, B, ldb, C, ldc, (int)N);
+  const int sms = P->sm_count;
+  if (D.n_segs > 0 || (!vbrc && D.n_blks > 0)) {
+    const size_t smem = (size_t)D.spmm.rows_max * NT * 4 + ((size_t)D.spmm.rows_max + 1) * 4;
+    if (V == 4)
+      vbrc ? launch_structured<4, true>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st)
+           : launch_structured<4, false>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st);
+    else if (V == 2)
+      vbrc ? launch_structured<2, true>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st)
+           : launch_structured<2, false>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st);
+    else
+      vbrc ? launch_structured<1, true>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st)
+           : launch_structured<1, false>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(P, e);
   }
+  const bool deep = P->tiling.spmm_depth == 8;   // 8 B rows in flight per warp
+  if (V == 4 && deep) launch_rows<4, 8>(D, B, ldb, C, ldc, (int)N, gy, sms, st);
+  else if (V == 4) launch_rows<4, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, st);
+  else if (V == 2) launch_rows<2, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, st);
+  else launch_rows<1, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, st);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SABLE_OK : cuda_fail(P, e);
 }

@@ -86,6 +86,8 @@ struct DevHybrid {
   const uint16_t *vbr_bf16_lo = nullptr;
   const float *vbr_scale = nullptr;  // per block power-of-two scale
   int32_t n_tc = 0;                  // (block, 128-row tile) pairs for the tensor-core path
+  int32_t n_segs = 0, n_blks = 0;
+  const uint8_t *row_pre = nullptr;  // per row: 1 if a VDIA segment or VBR block covers it (else null)
   const int32_t *rp = nullptr;   // CSR remainder row pointer (m + 1)
   const int32_t *ci = nullptr;   // padded by kCsrPad entries
   const float *cv = nullptr;     // padded by kCsrPad entries

@@ -219,7 +219,10 @@ sable_status sable_plan_reset(sable_plan_t plan);
  * upload.  spmv_rows: rows of an SpMV tile, a multiple of 4 in [4, 1024];
  * spmv_bytes: target algorithmic bytes per SpMV tile; spmm_rows: rows of an
  * SpMM tile, a multiple of 4 in [4, 256]; spmm_elems: target stored cells +
- * entries per SpMM tile.  Errors: SABLE_ERR_INVALID. */
+ * entries per SpMM tile.  The SpMM tiles serve the grouped launches of
+ * sable_batch_spmm; one matrix's SpMM is row split (a warp per row) and
+ * depends only on the column panel and depth below.  Errors:
+ * SABLE_ERR_INVALID. */
 sable_status sable_plan_set_tiling(sable_plan_t plan, int32_t spmv_rows, int64_t spmv_bytes,
                                    int32_t spmm_rows, int64_t spmm_elems);
 
@@ -230,7 +233,7 @@ typedef struct {
   int32_t spmm_rows;
   int64_t spmm_elems;
   int32_t spmm_cols;   /* 0 = widest panel the operands allow; else 32, 64 or 128 */
-  int32_t spmm_depth;  /* B rows in flight per warp in the SpMM CSR phase: 4 or 8 */
+  int32_t spmm_depth;  /* B rows in flight per warp in SpMM: 4 or 8 */
 } sable_tiling;
 sable_status sable_plan_get_tiling(sable_plan_t plan, sable_tiling *out);
 
@@ -243,10 +246,9 @@ sable_status sable_plan_get_tiling(sable_plan_t plan, sable_tiling *out);
  * effect at the next SpMM call.  Errors: SABLE_ERR_INVALID. */
 sable_status sable_plan_set_spmm_cols(sable_plan_t plan, int32_t cols);
 
-/* B rows each warp has in flight in the SpMM CSR phase: 4 (default) or 8
- * (more loads in flight, more registers: at most 4 CTAs per SM; used with
- * 128-column panels only).  Takes effect at the next SpMM call.  Errors:
- * SABLE_ERR_INVALID. */
+/* B rows each warp has in flight in SpMM: 4 (default) or 8 (more loads in
+ * flight, more registers: at most 4 CTAs per SM; used with 64- and 128-column
+ * panels).  Takes effect at the next SpMM call.  Errors: SABLE_ERR_INVALID. */
 sable_status sable_plan_set_spmm_depth(sable_plan_t plan, int32_t depth);
 
 /* Autotuner (no counterpart in the paper, which runs one generated kernel per
@@ -257,9 +259,9 @@ sable_status sable_plan_set_spmm_depth(sable_plan_t plan, int32_t depth);
  * C, m x N, row-major with leading dimension N); in / out are device buffers
  * the timed launches read and overwrite.  Candidates: SpMV rows {128, 256,
  * 512, 1024} x bytes {16K, 48K, 160K}, and 1024 rows with the bytes that cut
- * the plan into 1, 2 or 3 full waves of the CTAs the GPU holds at once; SpMM rows {8, 16, 32, 64} x cells
- * {1024, 4096, 16384} x (128 columns with 4 or 8 rows in flight, 64 columns);
- * the other op's tiling is kept.  Each candidate is
+ * the plan into 1, 2 or 3 full waves of the CTAs the GPU holds at once; SpMM
+ * (column panel, rows in flight) in {(128, 4), (128, 8), (64, 4), (64, 8),
+ * (32, 4)}; the other op's tiling is kept.  Each candidate is
  * uploaded (sable_plan_upload, which reallocates the plan's device tables and
  * waits for the device), run twice, then timed as the best of two rounds of
  * `reps` back-to-back launches.  The winner is remembered per shape class

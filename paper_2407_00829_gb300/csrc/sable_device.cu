@@ -73,10 +73,7 @@ template <> struct VecT<1> {
 
 // C[:, n0:n0+NT] for every item; V = 4 needs N, ldb, ldc multiples of 4 and
 // 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
-// Without CSRP the tile computes only its structured parts (VDIA, VBR), skips
-// tiles that have none, and stores only the rows they cover (A.row_pre); the
-// row-split kernel then adds the CSR remainder.
-template <int THREADS, int V, bool VBRC, int U = 4, bool CSRP = true>
+template <int THREADS, int V, bool VBRC, int U = 4>
 __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, const float *__restrict__ B,
                                           int64_t ldb, float *__restrict__ C, int64_t ldc, int N, float *cs,
                                           int *rps) {
@@ -89,7 +86,6 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
   const int lc = V * lane;                       // this lane's first column in the tile
   const bool lane_ok = n0 + lc < N;
   const unsigned n = (unsigned)A.n;
-  if (!CSRP && I.seg_lo == I.seg_hi && I.blk_lo == I.blk_hi) return;   // uniform over the CTA
   {
     const int r0 = I.r0, R = I.r1 - I.r0;
     for (int i = tid; i < R * NT; i += THREADS) cs[i] = 0.f;
@@ -162,7 +158,7 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
     __syncthreads();
 
     // ---- C. CSR remainder: the tile's entries split evenly over warps
-    const int pb = CSRP ? rps[0] : 0, pe = CSRP ? rps[R] : 0;
+    const int pb = rps[0], pe = rps[R];
     const int per = (pe - pb + NW - 1) / NW;
     const int pa = pb + warp * per, pz = min(pe, pa + per);
     if (pa < pz) {
@@ -214,7 +210,6 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
     // ---- store the tile
     if (lane_ok) {
       for (int i = warp; i < R; i += NW) {
-        if (!CSRP && !A.row_pre[r0 + i]) continue;
         const float *src = cs + i * NT + lc;
         float *dst = C + (int64_t)(r0 + i) * ldc + n0 + lc;
         if (V == 4) {
@@ -232,7 +227,8 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
 
 // C[:, n0:n0+NT] of one matrix; V = 4 needs N, ldb, ldc multiples of 4 and
 // 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
-template <int THREADS, int V, bool VBRC, int U = 4, bool CSRP = true>
+// Many-matrix and tiled form above; one matrix takes the row-split form below.
+template <int THREADS, int V, bool VBRC, int U = 4>
 __global__ void __launch_bounds__(THREADS, U == 8 ? 4 : 5)
 spmm_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ B, int64_t ldb,
                    float *__restrict__ C, int64_t ldc, int N) {
@@ -241,35 +237,122 @@ spmm_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict_
   int *rps = reinterpret_cast<int *>(cs + A.spmm.rows_max * 32 * V);
   for (int it = blockIdx.x; it < A.spmm.n; it += gridDim.x) {
     const DevItem I = A.spmm.items[it];
-    spmm_tile<THREADS, V, VBRC, U, CSRP>(A, I, B, ldb, C, ldc, N, cs, rps);
+    spmm_tile<THREADS, V, VBRC, U>(A, I, B, ldb, C, ldc, N, cs, rps);
   }
 }
 
-// CSR remainder of SpMM, row split: warp w of the grid owns rows w, w + W, ...
-// (consecutive rows on neighbouring warps), sums each row's entries in
-// registers with U rows of B in flight, and stores the row once, adding what
-// the structured launches left in C where A.row_pre marks the row.  No shared
-// memory and no barriers: the tiled form's per-tile barriers (zero the tile,
-// sum, store) held its B-row gathers to ~60 % of the device's row-gather rate.
-// The inner loop is kept short (it is issue-bound otherwise): whole groups of
-// U entries run unchecked, and the last group's missing entries gather row 0
-// (always present) and are left out of the sum by a warp-uniform test.  FULL:
-// every lane's columns lie inside N (no per-lane test).
-template <int V, int U, bool FULL>
-__device__ __forceinline__ void spmm_rows_run(const DevHybrid &A, const float *__restrict__ B, int ldb,
-                                              float *__restrict__ C, int ldc, int N, int n0) {
+// acc += sum over the cnt (1..32) entries held by lanes 0..cnt-1 (value v,
+// column c; the lanes past cnt hold c = 0, a row that always exists) of v x
+// the lane's columns of B row c, U rows of B in flight.  Whole groups of U
+// run unchecked; the last group leaves its missing entries out of the sum by
+// a warp-uniform test.
+template <int V, int U>
+__device__ __forceinline__ void rows_chunk(typename VecT<V>::T &acc, float v, int c, int cnt,
+                                           const float *__restrict__ Bl, int ldb, bool lane_ok) {
+  using Vt = VecT<V>;
+  using T = typename Vt::T;
+  int j = 0;
+  for (; j + U <= cnt; j += U) {
+    T bj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int cu = __shfl_sync(kFull, c, j + u);
+      bj[u] = lane_ok ? Vt::load(Bl + (int64_t)cu * ldb) : Vt::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) Vt::fma(acc, __shfl_sync(kFull, v, j + u), bj[u]);
+  }
+  if (j < cnt) {   // j + u <= 31
+    T bj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int cu = __shfl_sync(kFull, c, j + u);
+      bj[u] = lane_ok ? Vt::load(Bl + (int64_t)cu * ldb) : Vt::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float vu = __shfl_sync(kFull, v, j + u);
+      if (j + u < cnt) Vt::fma(acc, vu, bj[u]);
+    }
+  }
+}
+
+// SpMM, row split: warp w of the grid owns rows w, w + W, ... (consecutive rows
+// on the warps of one CTA) and sums each row in registers from one stream of
+// entries: the row's VDIA diagonals (columns r + off_lo + k, values strided by
+// the segment's run length), its FP32 block columns (columns c0 + k, values
+// strided by the block's height), then its CSR entries; it stores the row
+// once.  Neighbouring warps walk neighbouring rows of a segment or block at
+// about the same time, so their B rows and strided values are shared in L1.
+// tc: the blocks were multiplied on the tensor cores, which stored their rows
+// of C; the row adds that stored sum instead of the block's entries.  No
+// shared memory and no barriers (the tiled form's per-tile barriers held its
+// B-row gathers to ~60 % of the device's row-gather rate).  FULL: N is a
+// multiple of the panel width 32 V (no per-lane column test).  GEN: the
+// matrix has VDIA segments, or blocks summed here; without it every covering
+// part is a tensor-core block and the row only tests whether it has one.
+template <int V, int U, bool FULL, bool GEN>
+__global__ void __launch_bounds__(256, U == 8 ? 4 : 5)
+spmm_rows_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ B, int ldb,
+                 float *__restrict__ C, int ldc, int N, int tc) {
   using Vt = VecT<V>;
   using T = typename Vt::T;
   const int lane = threadIdx.x & 31;
+  const int n0 = blockIdx.y * 32 * V;
   const int lc = V * lane;
   const bool lane_ok = FULL || n0 + lc < N;
   const float *Bl = B + n0 + lc;
+  const int n = A.n;
   const int W = gridDim.x * (blockDim.x >> 5);
   for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < A.m; r += W) {
-    const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
-    const bool pre = A.row_pre != nullptr && A.row_pre[r] != 0;
-    if (pre && p0 == p1) continue;   // the structured launch already stored the whole row
     T acc = Vt::zero();
+    bool pre = false;   // C holds the row's tensor-core sum
+    if constexpr (GEN) {
+      bool own = false;
+      const int q1 = __ldg(A.srp + r + 1);
+      for (int q = __ldg(A.srp + r); q < q1; ++q) {   // the segments and blocks covering the row
+        const int ref = __ldg(A.sref + q);
+        const float *vp;
+        int stride, cb, kb, k1;   // entries kb .. k1 - 1: value vp[k * stride], column cb + k
+        if (ref & 1) {
+          if (tc) {
+            pre = true;
+            continue;
+          }
+          const DevBlk b = A.blks[ref >> 1];
+          vp = A.vbr + b.val_off + (r - b.r0);
+          stride = b.nr;
+          cb = b.c0;
+          kb = 0;
+          k1 = b.nc;
+        } else {
+          const DevSeg sg = A.segs[ref >> 1];
+          vp = A.vdia + sg.val_off + (r - sg.base);
+          stride = sg.ld;
+          cb = r + sg.off_lo;   // columns kept inside [0, n)
+          kb = max(0, -cb);
+          k1 = min(sg.ndiag, n - cb);
+        }
+        own = true;
+        for (; kb < k1; kb += 32) {
+          const int k = kb + lane;
+          float v = 0.f;
+          int c = 0;
+          if (k < k1) {
+            v = __ldg(vp + (int64_t)k * stride);
+            c = cb + k;
+          }
+          rows_chunk<V, U>(acc, v, c, min(32, k1 - kb), Bl, ldb, lane_ok);
+        }
+      }
+      if (pre && !own && __ldg(A.rp + r) == __ldg(A.rp + r + 1)) continue;   // stored whole by the tensor cores
+    } else {
+      // every covering part is a tensor-core block: a row with one and no
+      // CSR entries is already stored whole
+      if (A.srp != nullptr && __ldg(A.srp + r) < __ldg(A.srp + r + 1) && __ldg(A.rp + r) == __ldg(A.rp + r + 1))
+        continue;
+    }
+    const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
     for (int base = p0; base < p1; base += 32) {
       const int p = base + lane;
       float v = 0.f;
@@ -278,46 +361,15 @@ __device__ __forceinline__ void spmm_rows_run(const DevHybrid &A, const float *_
         v = __ldcs(A.cv + p);
         c = __ldcs(A.ci + p);
       }
-      const int cnt = min(32, p1 - base);
-      int j = 0;
-      for (; j + U <= cnt; j += U) {
-        T bj[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int cu = __shfl_sync(kFull, c, j + u);
-          bj[u] = lane_ok ? Vt::load(Bl + (int64_t)cu * ldb) : Vt::zero();
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) Vt::fma(acc, __shfl_sync(kFull, v, j + u), bj[u]);
-      }
-      if (j < cnt) {   // j + u <= 31: the lanes past the row's end hold c = 0
-        T bj[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int cu = __shfl_sync(kFull, c, j + u);
-          bj[u] = lane_ok ? Vt::load(Bl + (int64_t)cu * ldb) : Vt::zero();
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const float vu = __shfl_sync(kFull, v, j + u);
-          if (j + u < cnt) Vt::fma(acc, vu, bj[u]);
-        }
-      }
+      rows_chunk<V, U>(acc, v, c, min(32, p1 - base), Bl, ldb, lane_ok);
     }
     if (lane_ok) {
       float *dst = C + (int64_t)r * ldc + n0 + lc;
-      if (pre) Vt::fma(acc, 1.0f, Vt::load_once(dst));   // exact add of the structured part
+      if constexpr (!GEN) pre = A.srp != nullptr && __ldg(A.srp + r) < __ldg(A.srp + r + 1);
+      if (pre) Vt::fma(acc, 1.0f, Vt::load_once(dst));   // exact add of the stored block sum
       Vt::store_once(dst, acc);
     }
   }
-}
-
-// FULL when N is a multiple of the panel width 32 V.
-template <int V, int U, bool FULL>
-__global__ void __launch_bounds__(256, U == 8 ? 4 : 5)
-spmm_rows_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ B, int ldb,
-                 float *__restrict__ C, int ldc, int N) {
-  spmm_rows_run<V, U, FULL>(A, B, ldb, C, ldc, N, blockIdx.y * 32 * V);
 }
 
 // Many matrices in one launch (B_i: n_i x N, C_i: m_i x N, both with leading
@@ -437,7 +489,7 @@ struct Staging {
   std::vector<uint16_t> vbr_bf16, vbr_bf16_mid, vbr_bf16_lo;
   std::vector<float> vbr_scale;
   std::vector<float> cv, pcv;
-  std::vector<uint8_t> row_pre;
+  std::vector<int32_t> srp, sref;
   HostItems it_v, it_m, pit_v, pit_m;
 };
 
@@ -518,10 +570,21 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
       }
       if (!shared_rows) vbr_tc_pairs(H.blks, 0, S->tc_pairs);
     }
-    if (!H.segs.empty() || !H.blks.empty()) {   // rows a structured part covers
-      S->row_pre.assign(P->m, 0);
-      for (const Segment &g : H.segs) std::fill(S->row_pre.begin() + g.row0, S->row_pre.begin() + g.row0 + g.nrows, 1);
-      for (const Block &b : H.blks) std::fill(S->row_pre.begin() + b.r0, S->row_pre.begin() + b.r0 + b.nr, 1);
+    if (!H.segs.empty() || !H.blks.empty()) {   // per row: the segments and blocks covering it
+      S->srp.assign(P->m + 1, 0);
+      for (const Segment &g : H.segs)
+        for (int64_t r = g.row0; r < g.row0 + g.nrows; ++r) ++S->srp[r + 1];
+      for (const Block &b : H.blks)
+        for (int64_t r = b.r0; r < b.r0 + b.nr; ++r) ++S->srp[r + 1];
+      for (int64_t r = 0; r < P->m; ++r) S->srp[r + 1] += S->srp[r];
+      S->sref.resize(S->srp[P->m]);
+      std::vector<int32_t> at(S->srp.begin(), S->srp.end() - 1);
+      for (size_t i = 0; i < H.segs.size(); ++i)
+        for (int64_t r = H.segs[i].row0; r < H.segs[i].row0 + H.segs[i].nrows; ++r)
+          S->sref[at[r]++] = (int32_t)(i << 1);
+      for (size_t i = 0; i < H.blks.size(); ++i)
+        for (int64_t r = H.blks[i].r0; r < H.blks[i].r0 + H.blks[i].nr; ++r)
+          S->sref[at[r]++] = (int32_t)((i << 1) | 1);
     }
     S->rp.assign(H.crp.begin(), H.crp.end());
     S->ci.assign(H.cci.begin(), H.cci.end());
@@ -563,7 +626,8 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   const size_t o_prp = ar.add(S->prp.data(), vec_bytes(S->prp));
   const size_t o_pci = ar.add(S->pci.data(), vec_bytes(S->pci));
   const size_t o_pcv = ar.add(S->pcv.data(), vec_bytes(S->pcv));
-  const size_t o_pre = ar.add(S->row_pre.data(), vec_bytes(S->row_pre));
+  const size_t o_srp = ar.add(S->srp.data(), vec_bytes(S->srp));
+  const size_t o_sref = ar.add(S->sref.data(), vec_bytes(S->sref));
   size_t o_it[4][6];
   HostItems *its[4] = {&S->it_v, &S->it_m, &S->pit_v, &S->pit_m};
   for (int k = 0; k < 4; ++k) {
@@ -622,7 +686,8 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   D.err = reinterpret_cast<int32_t *>(blob + o_err);
   D.n_segs = (int32_t)S->segs.size();
   D.n_blks = (int32_t)S->blks.size();
-  D.row_pre = S->row_pre.empty() ? nullptr : reinterpret_cast<const uint8_t *>(blob + o_pre);
+  D.srp = S->srp.empty() ? nullptr : reinterpret_cast<const int32_t *>(blob + o_srp);
+  D.sref = S->srp.empty() ? nullptr : reinterpret_cast<const int32_t *>(blob + o_sref);
   D.spmv = items_of(0, its[0]);
   D.spmm = items_of(1, its[1]);
   DevHybrid &Q = P->dev_plain;
@@ -689,26 +754,18 @@ sable_status check_ready(sable_plan_t P) {
   return SABLE_OK;
 }
 
-template <int V, bool VBRC>
-void launch_structured(const DevHybrid &D, const float *B, int64_t ldb, float *C, int64_t ldc, int N, size_t smem,
-                       int gy, int sms, cudaStream_t st) {
-  auto k = spmm_hybrid_kernel<256, V, VBRC, 4, false>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid(grid_for(k, 256, smem, D.spmm.n, sms), gy);
-  k<<<grid, 256, smem, st>>>(D, B, ldb, C, ldc, N);
-}
-
 template <int V, int U>
 void launch_rows(const DevHybrid &D, const float *B, int64_t ldb, float *C, int64_t ldc, int N, int gy, int sms,
-                 cudaStream_t st) {
-  auto k = N % (32 * V) == 0 ? spmm_rows_kernel<V, U, true> : spmm_rows_kernel<V, U, false>;
+                 bool tc, cudaStream_t st) {
+  const bool full = N % (32 * V) == 0, gen = D.n_segs > 0 || (D.n_blks > 0 && !tc);
+  auto k = gen ? (full ? spmm_rows_kernel<V, U, true, true> : spmm_rows_kernel<V, U, false, true>)
+               : (full ? spmm_rows_kernel<V, U, true, false> : spmm_rows_kernel<V, U, false, false>);
   dim3 grid(grid_for(k, 256, 0, (D.m + 7) / 8, sms), gy);
-  k<<<grid, 256, 0, st>>>(D, B, (int)ldb, C, (int)ldc, N);
+  k<<<grid, 256, 0, st>>>(D, B, (int)ldb, C, (int)ldc, N, tc ? 1 : 0);
 }
 
-// C = A B after the tensor-core blocks (vbrc: their rows of C are stored):
-// the structured launch (VDIA, FP32 blocks) stores the rows those parts
-// cover, then the row-split launch adds the CSR remainder to every row.
+// C = A B in one row-split launch (after the tensor-core blocks when vbrc:
+// their rows of C are stored).
 sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int64_t N, int64_t ldb,
                          float *C, int64_t ldc, bool vbrc, cudaStream_t st) {
   if (N < 1 || ldb < N || ldc < N || N > (int64_t)65535 * 32 || ldb > INT32_MAX || ldc > INT32_MAX)
@@ -722,28 +779,14 @@ sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int
   // column panel per CTA: 128 (float4 lanes), 64 (float2) or 32
   const int cols = P->tiling.spmm_cols;
   const int V = cols == 32 ? 1 : cols == 64 ? (vec2 ? 2 : 1) : (vec ? 4 : 1);
-  const int NT = 32 * V;
-  const int gy = (int)((N + NT - 1) / NT);
+  const int gy = (int)((N + 32 * V - 1) / (32 * V));
   const int sms = P->sm_count;
-  if (D.n_segs > 0 || (!vbrc && D.n_blks > 0)) {
-    const size_t smem = (size_t)D.spmm.rows_max * NT * 4 + ((size_t)D.spmm.rows_max + 1) * 4;
-    if (V == 4)
-      vbrc ? launch_structured<4, true>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st)
-           : launch_structured<4, false>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st);
-    else if (V == 2)
-      vbrc ? launch_structured<2, true>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st)
-           : launch_structured<2, false>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st);
-    else
-      vbrc ? launch_structured<1, true>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st)
-           : launch_structured<1, false>(D, B, ldb, C, ldc, (int)N, smem, gy, sms, st);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(P, e);
-  }
   const bool deep = P->tiling.spmm_depth == 8;   // 8 B rows in flight per warp
-  if (V == 4 && deep) launch_rows<4, 8>(D, B, ldb, C, ldc, (int)N, gy, sms, st);
-  else if (V == 4) launch_rows<4, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, st);
-  else if (V == 2) launch_rows<2, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, st);
-  else launch_rows<1, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, st);
+  if (V == 4 && deep) launch_rows<4, 8>(D, B, ldb, C, ldc, (int)N, gy, sms, vbrc, st);
+  else if (V == 4) launch_rows<4, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, vbrc, st);
+  else if (V == 2 && deep) launch_rows<2, 8>(D, B, ldb, C, ldc, (int)N, gy, sms, vbrc, st);
+  else if (V == 2) launch_rows<2, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, vbrc, st);
+  else launch_rows<1, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, vbrc, st);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SABLE_OK : cuda_fail(P, e);
 }

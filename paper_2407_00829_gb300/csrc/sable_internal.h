@@ -87,7 +87,11 @@ struct DevHybrid {
   const float *vbr_scale = nullptr;  // per block power-of-two scale
   int32_t n_tc = 0;                  // (block, 128-row tile) pairs for the tensor-core path
   int32_t n_segs = 0, n_blks = 0;
-  const uint8_t *row_pre = nullptr;  // per row: 1 if a VDIA segment or VBR block covers it (else null)
+  // per row, the VDIA segments and VBR blocks covering it: refs srp[r] ..
+  // srp[r + 1] - 1 of sref, each (index << 1) | (1 for a block); null when
+  // the matrix has neither
+  const int32_t *srp = nullptr;
+  const int32_t *sref = nullptr;
   const int32_t *rp = nullptr;   // CSR remainder row pointer (m + 1)
   const int32_t *ci = nullptr;   // padded by kCsrPad entries
   const float *cv = nullptr;     // padded by kCsrPad entries
@@ -108,7 +112,7 @@ struct Tiling {
   int32_t rows_per_item_mm = 32; // SpMM row tile (<= 256, multiple of 4)
   int64_t item_elems_mm = 4096;  // stored cells + entries per SpMM tile
   int32_t spmm_cols = 0;         // SpMM column panel per CTA: 0 = widest the operands allow, 32, 64, 128
-  int32_t spmm_depth = 4;        // SpMM CSR phase: B rows in flight per warp (4 or 8; 8 with 128 columns)
+  int32_t spmm_depth = 4;        // SpMM CSR phase: B rows in flight per warp (4 or 8; 8 with 64 or 128 columns)
 };
 
 // Host-side extracted hybrid form and its device mirror.

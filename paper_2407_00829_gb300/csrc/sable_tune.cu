@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "sable_internal.h"
@@ -142,12 +143,9 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
       }
       (void)cudaGetLastError();
     } else {
-      for (int32_t rows : {8, 16, 32, 64})
-        for (int64_t elems : {1024, 4096, 16384}) {
-          cand.push_back({cur.spmv_rows, cur.spmv_bytes, rows, elems, 128, 4});
-          cand.push_back({cur.spmv_rows, cur.spmv_bytes, rows, elems, 128, 8});
-          cand.push_back({cur.spmv_rows, cur.spmv_bytes, rows, elems, 64, 4});
-        }
+      // one matrix's SpMM is row split: only the column panel and depth matter
+      for (const auto &cd : {std::pair<int32_t, int32_t>{128, 4}, {128, 8}, {64, 4}, {64, 8}, {32, 4}})
+        cand.push_back({cur.spmv_rows, cur.spmv_bytes, cur.spmm_rows, cur.spmm_elems, cd.first, cd.second});
     }
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -43,7 +43,7 @@ def test_autotune_spmv_and_spmm():
     for op, tol in ((sable.TUNE_SPMM_FP32, 1e-5), (sable.TUNE_SPMM_BF16, 2e-2)):
         tm, msm = P.autotune(op, B, C, reps=3)
         assert tm["spmm_rows"] in SPMM_ROWS and tm["spmm_elems"] in SPMM_ELEMS
-        assert (tm["spmm_cols"], tm["spmm_depth"]) in ((128, 4), (128, 8), (64, 4))
+        assert (tm["spmm_cols"], tm["spmm_depth"]) in ((128, 4), (128, 8), (64, 4), (64, 8), (32, 4))
         assert msm > 0
         assert (tm["spmv_rows"], tm["spmv_bytes"]) == (t["spmv_rows"], t["spmv_bytes"])   # SpMV choice kept
         C.fill_(float("nan"))

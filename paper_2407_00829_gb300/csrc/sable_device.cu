@@ -71,8 +71,11 @@ template <> struct VecT<1> {
   __device__ static void atomic_add_to(float *p, const T &a) { atomicAdd(p, a); }
 };
 
-// C[:, n0:n0+NT] for every item; V = 4 needs N, ldb, ldc multiples of 4 and
-// 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
+// Tiled SpMM, the form of the grouped many-matrix launch (one matrix's SpMM
+// is row split, below): C[r0:r1, n0:n0+NT] of one row tile, its parts summed
+// into a shared tile and stored once.  V = 4 needs N, ldb, ldc multiples of 4
+// and 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row
+// pointers.
 template <int THREADS, int V, bool VBRC, int U = 4>
 __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, const float *__restrict__ B,
                                           int64_t ldb, float *__restrict__ C, int64_t ldc, int N, float *cs,
@@ -227,20 +230,6 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
 
 // C[:, n0:n0+NT] of one matrix; V = 4 needs N, ldb, ldc multiples of 4 and
 // 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
-// Many-matrix and tiled form above; one matrix takes the row-split form below.
-template <int THREADS, int V, bool VBRC, int U = 4>
-__global__ void __launch_bounds__(THREADS, U == 8 ? 4 : 5)
-spmm_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ B, int64_t ldb,
-                   float *__restrict__ C, int64_t ldc, int N) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float *cs = reinterpret_cast<float *>(smem_raw);
-  int *rps = reinterpret_cast<int *>(cs + A.spmm.rows_max * 32 * V);
-  for (int it = blockIdx.x; it < A.spmm.n; it += gridDim.x) {
-    const DevItem I = A.spmm.items[it];
-    spmm_tile<THREADS, V, VBRC, U>(A, I, B, ldb, C, ldc, N, cs, rps);
-  }
-}
-
 // acc += sum over the cnt (1..32) entries held by lanes 0..cnt-1 (value v,
 // column c; the lanes past cnt hold c = 0, a row that always exists) of v x
 // the lane's columns of B row c, U rows of B in flight.  Whole groups of U

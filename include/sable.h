@@ -157,8 +157,13 @@ sable_status sable_plan_upload(sable_plan_t plan, void *stream);
 sable_status sable_spmv(sable_plan_t plan, const float *x, float *y, void *stream);
 
 /* C := A B.  B: device, n x N row-major with leading dimension ldb >= N;
- * C: device, m x N row-major, ldc >= N (overwritten).  N >= 1.
- * SABLE_BF16_BLOCKS as documented at sable_precision. */
+ * C: device, m x N row-major, ldc >= N (overwritten).  1 <= N <= 65535 * 32;
+ * ldb, ldc <= INT32_MAX.  SABLE_BF16_BLOCKS / SABLE_FP32_SPLIT as documented
+ * at sable_precision: the tensor-core launch stores the blocks' rows of C,
+ * then one row-split launch adds each row's VDIA diagonals, FP32 blocks and
+ * CSR entries.  VBR blocks of different stages that share rows stay on the
+ * FP32 path in every precision.  Errors: SABLE_ERR_ORDER before upload;
+ * SABLE_ERR_INVALID; SABLE_ERR_CUDA. */
 sable_status sable_spmm(sable_plan_t plan, const float *B, int64_t N, int64_t ldb, float *C,
                         int64_t ldc, sable_precision prec, void *stream);
 

@@ -20,6 +20,9 @@ Data set work flow (matrices from ``synth.planner_set_matrix``):
                         the device features; write features + timings
   evaluate (device)     train on the first matrices, score on the held-out
                         rest: plan-quality loss t_chosen / t_exhaustive - 1
+  select   (device)     as evaluate, after choosing the ensemble size, steps
+                        and learning rate on a validation part of the
+                        training matrices
 """
 from __future__ import annotations
 
@@ -110,17 +113,23 @@ def matrix_features(A, device="cuda") -> np.ndarray:
     return features(A["m"], A["n"], row, col).cpu().numpy()
 
 
-def _time_ms(fn, reps=20, warm=3):
+def _time_ms(fn, reps=20, warm=3, rounds=3):
+    """Mean device ms of one launch over `reps` back-to-back launches, best of
+    `rounds` (events around each launch would also time the host's launch
+    gaps, a large and noisy share of a tens-of-microseconds SpMV)."""
     import torch
     for _ in range(warm):
         fn()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-    for a, b in ev:
+    best = float("inf")
+    for _ in range(rounds):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        fn()
+        for _ in range(reps):
+            fn()
         b.record()
-    torch.cuda.synchronize()
-    return float(np.median([a.elapsed_time(b) for a, b in ev]))
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b) / reps)
+    return best
 
 
 def time_plan(P, A, x, y, B, C):
@@ -268,7 +277,7 @@ def quality(times, picks):
     return np.array([[times[i, picks[i, o], o] / times[i, :, o].min() - 1 for o in range(O)] for i in range(M)])
 
 
-def evaluate(data, n_test=200, steps=2000, seed=0, lp=None):
+def evaluate(data, n_test=200, steps=2000, seed=0, lp=None, members=5, lr=2e-3):
     """Train on all but the last n_test matrices (unless a trained planner is
     given) and compare on those: the learned planner, the fixed default plan,
     CSR only and the best single candidate on the training matrices."""
@@ -278,8 +287,8 @@ def evaluate(data, n_test=200, steps=2000, seed=0, lp=None):
     cut = M - n_test
     res = {"train_matrices": int(cut), "test_matrices": int(n_test)}
     if lp is None:
-        lp = LearnedPlanner(seed=seed)
-        res["train_mse"] = float(np.mean(lp.fit(X[:cut * n_ops], Y[:cut * n_ops], steps=steps)))
+        lp = LearnedPlanner(seed=seed, members=members)
+        res["train_mse"] = float(np.mean(lp.fit(X[:cut * n_ops], Y[:cut * n_ops], steps=steps, lr=lr)))
     T = data["times"]
     test = T[cut:]
     learned = lp.choose(X[cut * n_ops:]).reshape(n_test, n_ops)
@@ -300,9 +309,35 @@ def evaluate(data, n_test=200, steps=2000, seed=0, lp=None):
     return res, lp
 
 
+GRID = [dict(members=m, steps=st, lr=lr) for m in (5, 9) for st in (2000, 4000) for lr in (1e-3, 2e-3)]
+
+
+def select(data, n_test=200, n_val=80, seed=0, grid=GRID):
+    """Model selection without the held-out matrices: each setting is trained
+    on the training matrices but the last n_val and scored on those (mean
+    plan-quality loss over the ops); the best setting is then trained on all
+    training matrices and evaluated once on the held-out n_test."""
+    X, Y = design(data)
+    n_ops = len(OPS)
+    M = data["features"].shape[0]
+    cut = M - n_test
+    fit_n = cut - n_val
+    T = data["times"]
+    scores = []
+    for g in grid:
+        lp = LearnedPlanner(seed=seed, members=g["members"])
+        lp.fit(X[:fit_n * n_ops], Y[:fit_n * n_ops], steps=g["steps"], lr=g["lr"])
+        picks = lp.choose(X[fit_n * n_ops:cut * n_ops]).reshape(n_val, n_ops)
+        scores.append(float(quality(T[fit_n:cut], picks).mean()))
+    best = grid[int(np.argmin(scores))]
+    res, lp = evaluate(data, n_test=n_test, seed=seed, **best)
+    res["selection"] = {"validation_matrices": n_val, "grid": grid, "validation_loss": scores, "chosen": best}
+    return res, lp
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["regions", "collect", "evaluate"])
+    ap.add_argument("cmd", choices=["regions", "collect", "evaluate", "select"])
     ap.add_argument("--start", type=int, default=0)
     ap.add_argument("--stop", type=int, default=600)
     ap.add_argument("--seed", type=int, default=1005)
@@ -336,7 +371,7 @@ def main():
         d = {k: np.concatenate([p[k] for p in parts]) for k in ("features", "times", "meta")}
         order = np.argsort(d["meta"][:, 0], kind="stable")
         d = {k: v[order] for k, v in d.items()}
-        res, lp = evaluate(d, n_test=a.test, steps=a.steps)
+        res, lp = select(d, n_test=a.test) if a.cmd == "select" else evaluate(d, n_test=a.test, steps=a.steps)
         print(json.dumps(res))
         if a.out.endswith(".npz"):
             np.savez_compressed(a.out, names=np.array(NAMES), ops=np.array([o for o, _ in OPS]), **d)

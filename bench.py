@@ -2,8 +2,10 @@
 """Benchmark: hybrid VDIA+CSR SpMV on the 1M x 1M band + power-law workload.
 
 One step = one SpMV y = A x of the whole matrix through the library's single
-fused kernel launch (the extraction is the inspector, done once before the
-timed region, as in the paper's inspector-executor evaluation, Section 5).
+kernel launch over all regions (the extraction is the inspector, done once
+before the timed region, as in the paper's inspector-executor evaluation,
+Section 5).  The line also reports the 200k SpMM workload (row-split SpMM,
+tensor-core blocks) against plain CSR and cuSPARSE.
 Prints one JSON line.  Inputs are kept resident in HBM; the L2 cache is
 defeated by rotating over replicas of the matrix whose total size exceeds
 3 x L2, so every launch streams its matrix from HBM.

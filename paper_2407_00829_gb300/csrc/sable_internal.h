@@ -112,7 +112,7 @@ struct Tiling {
   int32_t rows_per_item_mm = 32; // SpMM row tile (<= 256, multiple of 4)
   int64_t item_elems_mm = 4096;  // stored cells + entries per SpMM tile
   int32_t spmm_cols = 0;         // SpMM column panel per CTA: 0 = widest the operands allow, 32, 64, 128
-  int32_t spmm_depth = 4;        // SpMM CSR phase: B rows in flight per warp (4 or 8; 8 with 64 or 128 columns)
+  int32_t spmm_depth = 4;        // SpMM: B rows in flight per warp (4 or 8; 8 with 64 or 128 columns)
 };
 
 // Host-side extracted hybrid form and its device mirror.

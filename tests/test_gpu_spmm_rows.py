@@ -1,7 +1,8 @@
-"""SpMM through the structured launch plus the row-split CSR launch: rows
-that several parts cover, rows no part covers, matrices without a CSR
-remainder, odd widths and several column panels, and VBR blocks of two
-stages that share rows (those stay on the FP32 path in every precision)."""
+"""SpMM through the row-split launch (after the tensor-core launch for BF16
+and three-term blocks): rows that several parts cover, rows no part covers,
+matrices without a CSR remainder, odd widths and several column panels, and
+VBR blocks of two stages that share rows (those stay on the FP32 path in
+every precision)."""
 import numpy as np
 import pytest
 

@@ -66,3 +66,40 @@ def test_committed_weights_through_the_reference_mlp():
         for name, c in fixed.items():
             qf = pl.quality(T[cut:], np.full((N_TEST, O), c[o]))
             assert q[:, o].mean() < qf[:, o].mean(), (op, name)
+
+
+def test_model_selection_never_sees_the_held_out_matrices(monkeypatch):
+    """planner.select scores its grid on a validation part of the training
+    matrices and trains the chosen setting on the training matrices only (a
+    stand-in for the device-trained ensemble records what each fit sees)."""
+    d = _data()
+    M, O = d["features"].shape[0], len(pl.OPS)
+    fits = []
+
+    class Fake:
+        def __init__(self, seed=0, members=5, hidden=64):
+            self.members = members
+
+        def fit(self, X, Y, steps=2000, lr=2e-3):
+            fits.append((X.shape[0], self.members, steps, lr, X.copy()))
+            return [0.0]
+
+        def choose(self, X):   # a rule that depends on the inputs: the candidate of the largest feature
+            return np.argmax(X[:, : len(pl.NAMES)], axis=1)
+
+    monkeypatch.setattr(pl, "LearnedPlanner", Fake)
+    X, _ = pl.design(d)
+    n_val = 80
+    res, _ = pl.select(d, n_test=N_TEST, n_val=n_val)
+    grid = pl.GRID
+    assert len(fits) == len(grid) + 1
+    for (rows, members, steps, lr, Xf), g in zip(fits, grid):
+        assert rows == (M - N_TEST - n_val) * O
+        assert (members, steps, lr) == (g["members"], g["steps"], g["lr"])
+        np.testing.assert_array_equal(Xf, X[:rows])
+    rows, members, steps, lr, Xf = fits[-1]
+    assert rows == (M - N_TEST) * O
+    np.testing.assert_array_equal(Xf, X[:rows])
+    chosen = res["selection"]["chosen"]
+    assert (members, steps, lr) == (chosen["members"], chosen["steps"], chosen["lr"])
+    assert chosen == grid[int(np.argmin(res["selection"]["validation_loss"]))]

@@ -192,3 +192,25 @@ def test_empty_matrix_plans():
         info = P.info()
         assert info["nnz"] == 0 and info["n_segments"] == 0 and info["n_blocks"] == 0
         P.close()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_library_recovers_separated_planted_blocks(seed):
+    """Ground truth, not the oracle: full blocks far apart in a sparse matrix
+    come back from the library's block extractor (with the candidate-region
+    pre-pass) exactly as planted, and so does a short wide block that only the
+    column-outer search of Algorithm 1 can find."""
+    rng = np.random.default_rng(400 + seed)
+    planted = [(4, 6, 20, 24), (60, 70, 30, 18), (120, 120, 25, 30)]
+    A = synth.assemble(rng, 160, 160, blocks=[(r0, c0, nr, nc, 1.0) for (r0, c0, nr, nc) in planted],
+                       n_scatter=150)
+    P = sable.plan_from(A, [(sable.VBR, dict(a_min=300, max_span=64, tile=8)), (sable.CSR, None)], upload=False)
+    assert sorted(map(tuple, P.blocks().tolist())) == sorted((r0, nr, c0, nc) for (r0, c0, nr, nc) in planted)
+    P.close()
+    r, c = np.nonzero(np.pad(np.ones((4, 60)), ((20, 26), (15, 15))))
+    A = dict(m=50, n=90, row=r, col=c, val=np.ones(r.size, dtype=np.float32))
+    for tile in (0, 8):
+        P = sable.plan_from(A, [(sable.VBR, dict(a_min=100, max_span=64, tile=tile)), (sable.CSR, None)],
+                            upload=False)
+        assert P.blocks().tolist() == [[20, 4, 15, 60]]
+        P.close()

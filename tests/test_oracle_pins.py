@@ -238,110 +238,180 @@ def test_find_block_bounded_by_brute_force(seed):
     sc2, o0, o1, i0, i1 = ox.find_block(R.rowlist, 0, m, 0, n, p)   # sc2: the score squared
     best = _brute_best(Mb, p.a_min, p.delta, ox._isqrt_ceil(p.a_min))
     assert sc2 <= best * best * (1 + 1e-12) + 1e-12
-    if sc2 >= 0:
-        a = (o1 - o0) * (i1 - i0)
-        z = int(Mb[o0:o1, i0:i1].sum())
-        assert math.isclose(math.sqrt(sc2), a * math.pow(z / a - p.delta, 1.5), rel_tol=1e-12, abs_tol=1e-12)
-        assert a >= p.a_min and z / a >= p.delta and o1 - o0 >= ox._isqrt_ceil(p.a_min)
-    else:
-        assert best < 0 or True
+    # every one of these matrices holds a delta-dense window (brute force finds
+    # one), and Algorithm 2 must return some window then
+    assert best > 0 and sc2 > 0
+    a = (o1 - o0) * (i1 - i0)
+    z = int(Mb[o0:o1, i0:i1].sum())
+    assert math.isclose(math.sqrt(sc2), a * math.pow(z / a - p.delta, 1.5), rel_tol=1e-12, abs_tol=1e-12)
+    assert a >= p.a_min and z / a >= p.delta and o1 - o0 >= ox._isqrt_ceil(p.a_min)
 
 
-@pytest.mark.parametrize("seed", range(5))
-def test_trim_is_a_local_optimum(seed):
-    rng = np.random.default_rng(200 + seed)
-    Mb = (rng.random((15, 15)) < 0.6).astype(np.int64)
+def _lines(Mb):
     r, c = np.nonzero(Mb)
-    R = ox.Residual(15, 15, r, c, np.arange(r.size))
-    r0, r1, c0, c1, z = ox.trim(R, 0, 15, 0, 15)
-    assert z == Mb[r0:r1, c0:c1].sum()
-    dens = z / ((r1 - r0) * (c1 - c0))
-    for (a, b, cc, dd) in [(r0 + 1, r1, c0, c1), (r0, r1 - 1, c0, c1),
-                           (r0, r1, c0 + 1, c1), (r0, r1, c0, c1 - 1)]:
-        if b > a and dd > cc:
-            assert Mb[a:b, cc:dd].sum() / ((b - a) * (dd - cc)) <= dens + 1e-15
+    return ox.Residual(Mb.shape[0], Mb.shape[1], r, c, np.arange(r.size))
 
 
-def _format_cells(ex, entries):
-    vd, vb, cs = {}, {}, {}
-    for (r0, nr, lo, nd) in ex.segments:
-        for r in range(r0, r0 + nr):
-            for o in range(lo, lo + nd):
-                c = r + o
-                if 0 <= c < ex.n:
-                    key = (r, c)
-                    vd[key] = entries[key][1] if key in entries and entries[key][0] == ox.VDIA else 0.0
-    for (r0, nr, c0, nc) in ex.blocks:
-        for r in range(r0, r0 + nr):
-            for c in range(c0, c0 + nc):
-                key = (r, c)
-                vb[key] = entries[key][1] if key in entries and entries[key][0] == ox.VBR else 0.0
-    for key, (o, v) in entries.items():
-        if o == ox.CSR:
-            cs[key] = v
-    return vd, vb, cs
+@pytest.mark.parametrize("m,n,span", [(20, 15, 64), (30, 8, 64), (40, 12, 25)])
+def test_find_block_all_ones_closed_form(m, n, span):
+    # Algorithm 2 on a region with every cell set: every window has density 1,
+    # so the score a (1 - delta)^1.5 grows with the area and the best window is
+    # the widest and tallest one the outer span cap allows, from the first start
+    R = _lines(np.ones((m, n), dtype=np.int64))
+    p = ox.Params(delta=0.5, a_min=36, max_span=span)
+    sc2, o0, o1, i0, i1 = ox.find_block(R.rowlist, 0, m, 0, n, p)
+    h = min(m, span)
+    a = h * n
+    assert (o0, o1, i0, i1) == (0, h, 0, n)
+    assert sc2 == pytest.approx((a * (1 - p.delta)) ** 3 / a, rel=1e-15)
+
+
+@pytest.mark.parametrize("r0,h,w,n", [(0, 12, 10, 30), (7, 10, 12, 25), (3, 20, 9, 9), (11, 16, 16, 40)])
+def test_find_block_planted_block_at_inner_start(r0, h, w, n):
+    # a full h x w block whose columns start at the region's first inner index:
+    # the window scan cannot carry empty columns in front of it, so Algorithm 2
+    # returns exactly the block, whose score is the brute-force maximum over
+    # every rectangle (adding empty cells lowers a (d - delta)^1.5 for d >= delta)
+    m = 40
+    Mb = np.zeros((m, n), dtype=np.int64)
+    Mb[r0:r0 + h, 0:w] = 1
+    p = ox.Params(delta=0.5, a_min=90, max_span=64)
+    sc2, o0, o1, i0, i1 = ox.find_block(_lines(Mb).rowlist, 0, m, 0, n, p)
+    assert (o0, o1, i0, i1) == (r0, r0 + h, 0, w)
+    brute = _brute_best(Mb, p.a_min, p.delta, ox._isqrt_ceil(p.a_min))
+    assert sc2 > 0 and math.isclose(math.sqrt(sc2), brute, rel_tol=1e-12)
+    assert math.isclose(math.sqrt(sc2), h * w * (1 - p.delta) ** 1.5, rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("r0,c0,h,w", [(5, 7, 12, 10), (20, 30, 15, 20), (3, 25, 20, 5), (30, 3, 10, 37)])
+def test_find_block_window_covers_planted_block_and_trim_recovers_it(r0, c0, h, w):
+    # elsewhere the literal window may keep empty columns or rows around the
+    # block (the sliding window of Algorithm 2 stops at the first dense
+    # window), but it always covers the block with a positive score, and Trim
+    # (Algorithm 1) strips exactly the empty lines back off
+    m, n = 60, 50
+    Mb = np.zeros((m, n), dtype=np.int64)
+    Mb[r0:r0 + h, c0:c0 + w] = 1
+    R = _lines(Mb)
+    p = ox.Params(delta=0.5, a_min=100, max_span=64)
+    for lines, O, I, (br0, br1, bc0, bc1) in ((R.rowlist, m, n, (r0, r0 + h, c0, c0 + w)),
+                                              (R.collist, n, m, (c0, c0 + w, r0, r0 + h))):
+        if br1 - br0 < ox._isqrt_ceil(p.a_min):
+            continue                     # block shorter than s_min along this search's outer axis
+        sc2, o0, o1, i0, i1 = ox.find_block(lines, 0, O, 0, I, p)
+        assert sc2 > 0
+        assert o0 <= br0 and br1 <= o1 and i0 <= bc0 and bc1 <= i1
+        win = (o0, o1, i0, i1) if lines is R.rowlist else (i0, i1, o0, o1)
+        assert ox.trim(R, *win) == (r0, r0 + h, c0, c0 + w, h * w)
+
+
+def test_candidate_regions_band_slabs_by_hand():
+    # A band of the 9 diagonals -4..4 over 200 rows, 8 x 8 cells, delta 0.5:
+    # a diagonal cell holds 5+6+7+8+8+7+6+5 = 52 >= 32 entries (hot), an
+    # off-diagonal cell 1+2+3+4 = 10 (cold), so the hot cells are (I, I) for
+    # I = 0..24, one 8-connected component of 25 cells in a 25 x 25 box
+    # (4 x 25 < 625: under a quarter full) and taller than S = 64 / 8 = 8 cell
+    # rows.  It is cut into slabs of 8 cell rows from its first row: cell rows
+    # [0,8), [8,16), [16,24), [24,25); each box is its cells' columns grown by
+    # one cell on each side, and grown outward in rows only at the first and
+    # last slab (clipped to the matrix); no two boxes overlap, so none merge.
+    m = 200
+    r, c = [], []
+    for i in range(m):
+        for d in range(-4, 5):
+            if 0 <= i + d < m:
+                r.append(i)
+                c.append(i + d)
+    R = ox.Residual(m, m, np.array(r), np.array(c), np.arange(len(r)))
+    p = ox.Params(delta=0.5, a_min=100, max_span=64, tile=8)
+    cells = [(0, 8, 0, 9), (8, 16, 7, 17), (16, 24, 15, 25), (24, 25, 23, 25)]
+    expect = [(8 * a, min(m, 8 * b), 8 * cc, min(m, 8 * d)) for (a, b, cc, d) in cells]
+    assert ox.candidate_regions(R, p) == expect
+
+
+def test_candidate_regions_band_inside_matrix_by_hand():
+    # the diagonals -4..4 over rows 40..159 of a 240 x 240 matrix: hot cells
+    # (I, I) for I = 5..19 (15 cells, box 15 x 15 = 225 > 4 x 15), taller
+    # than S = 8 cell rows, so two slabs: cell rows [5, 13) and [13, 20).  The
+    # first slab grows up by one cell row (to 4), the last down by one (to
+    # 21); columns are each slab's cells grown by one: [4, 14) and [12, 21).
+    m = 240
+    r, c = [], []
+    for i in range(40, 160):
+        for d in range(-4, 5):
+            r.append(i)
+            c.append(i + d)
+    R = ox.Residual(m, m, np.array(r), np.array(c), np.arange(len(r)))
+    p = ox.Params(delta=0.5, a_min=100, max_span=64, tile=8)
+    assert ox.candidate_regions(R, p) == [(32, 104, 32, 112), (104, 168, 96, 168)]
+
+
+def test_candidate_regions_tall_component_over_a_quarter_full_is_one_box():
+    # an L of full cells: columns 0..7 over all 200 rows (cells (I, 0), I =
+    # 0..24) and rows 192..199 over columns 0..23 (cells (24, 0..2)): 27 cells
+    # in a 25 x 3 box, 27 / 75 = 36 % >= a quarter, so no slab cut although it
+    # is taller than S: one box, grown by one cell and clipped: rows [0, 200),
+    # columns [0, 32)
+    m = n = 200
+    Mb = np.zeros((m, n), dtype=np.int64)
+    Mb[:, 0:8] = 1
+    Mb[192:200, 0:24] = 1
+    p = ox.Params(delta=0.5, a_min=100, max_span=64, tile=8)
+    assert ox.candidate_regions(_lines(Mb), p) == [(0, 200, 0, 32)]
+
+
+def test_candidate_regions_single_block_box_by_hand():
+    # one full 19 x 30 block, rows 17..35 and columns 41..70, of a 100 x 120
+    # matrix, 8 x 8 cells, delta 0.5 (hot: >= 32 of 64 entries).  Cell rows
+    # 2, 3, 4 hold 7, 8, 4 of its rows; cell columns 5, 6, 7, 8 hold 7, 8, 8, 7
+    # of its columns.  Hot: every cell of rows 2 and 3, and in row 4 the cells
+    # of columns 6 and 7 (4 x 8 = 32, exactly delta x area) but not 5 and 8
+    # (4 x 7 = 28).  One component, cell rows [2, 5) x columns [5, 9), grown
+    # by one cell: rows [8, 48), columns [32, 80).
+    m, n = 100, 120
+    Mb = np.zeros((m, n), dtype=np.int64)
+    Mb[17:36, 41:71] = 1
+    p = ox.Params(delta=0.5, a_min=100, max_span=64, tile=8)
+    assert ox.candidate_regions(_lines(Mb), p) == [(8, 48, 32, 80)]
+
+
+@pytest.mark.parametrize("tile", [0, 8])
+def test_short_wide_block_found_by_the_column_search(tile):
+    # 4 rows x 60 columns, a_min 100 (s_min = 10): a row-outer window needs 10
+    # rows, so its density is at most 4 / 10 < delta and the CSR search finds
+    # nothing; the CSC search (columns outer, 60 >= 10) finds the block, and
+    # Decompose must take it (Algorithm 1 keeps the better of the two)
+    m, n = 50, 90
+    Mb = np.zeros((m, n), dtype=np.int64)
+    Mb[20:24, 15:75] = 1
+    r, c = np.nonzero(Mb)
+    p = ox.Params(delta=0.5, a_min=100, max_span=64, tile=tile)
+    ex = ox.run_plan(m, n, r, c, np.ones(r.size, dtype=np.float32), [(ox.VBR, p), (ox.CSR, None)])
+    assert ex.blocks == [(20, 4, 15, 60)]
 
 
 @pytest.mark.parametrize("seed", range(3))
-def test_three_format_plan_partition_and_invariants(seed):
-    rng = np.random.default_rng(300 + seed)
-    m = 160
-    A = synth.assemble(rng, m, m, bands=[(o, 10, 120) for o in (-1, 0, 1)] + [(40, 0, 100)],
-                       blocks=[(100, 5, 24, 30, 0.85), (20, 120, 30, 20, 0.9)], n_scatter=300)
-    pv = ox.Params(delta=0.75, a_min=200, l_seg=16)
-    pb = ox.Params(delta=0.5, a_min=200, max_span=64, tile=8)
-    ex = ox.run_plan(m, m, A["row"], A["col"], A["val"], [(ox.VDIA, pv), (ox.VBR, pb), (ox.CSR, None)])
-    entries = {(int(i), int(j)): (int(o), v) for i, j, o, v in zip(ex.rows, ex.cols, ex.owner, ex.vals)}
-    ox.check_partition(ex, *_format_cells(ex, entries))
-    # VBR invariants (Algorithm 1): row- and column-disjoint, width >= 2, dense, large
-    for a, b in itertools.combinations(ex.blocks, 2):
-        assert a[0] + a[1] <= b[0] or b[0] + b[1] <= a[0]
-        assert a[2] + a[3] <= b[2] or b[2] + b[3] <= a[2]
-    for (r0, nr, c0, nc) in ex.blocks:
-        z = sum(1 for (i, j), (o, _) in entries.items() if o == ox.VBR and r0 <= i < r0 + nr and c0 <= j < c0 + nc)
-        assert nc >= 2 and nr * nc >= pb.a_min and z / (nr * nc) >= pb.delta
-    # VDIA invariants (Algorithms 3, 4): row-disjoint, long enough
-    rows_seen = set()
-    for (r0, nr, lo, nd) in ex.segments:
-        assert nr >= pv.l_seg
-        rr = set(range(r0, r0 + nr))
-        assert not (rr & rows_seen)
-        rows_seen |= rr
-    assert len(ex.segments) >= 1 and len(ex.blocks) == 2
-
-
-def test_partition_checker_catches_mistakes():
-    rng = np.random.default_rng(1)
-    A = synth.assemble(rng, 64, 64, bands=[(0, 0, 64), (1, 0, 64)], n_scatter=50)
-    ex = ox.run_plan(64, 64, A["row"], A["col"], A["val"],
-                     [(ox.VDIA, ox.Params(delta=0.75, a_min=50, l_seg=8)), (ox.CSR, None)])
-    entries = {(int(i), int(j)): (int(o), v) for i, j, o, v in zip(ex.rows, ex.cols, ex.owner, ex.vals)}
-    vd, vb, cs = _format_cells(ex, entries)
-    ox.check_partition(ex, vd, vb, cs)
-    k = next(iter(cs))
-    bad = dict(cs)
-    del bad[k]
-    with pytest.raises(AssertionError):
-        ox.check_partition(ex, vd, vb, bad)                  # dropped entry
-    bad = dict(cs)
-    bad[k] = np.float32(bad[k]) + np.float32(1.0)
-    with pytest.raises(AssertionError):
-        ox.check_partition(ex, vd, vb, bad)                  # changed value
-    kd = next(key for key in vd if vd[key] != 0)
-    bad = dict(cs)
-    bad[kd] = vd[kd]
-    with pytest.raises(AssertionError):
-        ox.check_partition(ex, vd, vb, bad)                  # entry held twice
-    kz = next((key for key in vd if vd[key] == 0), None)
-    if kz is not None:
-        badv = dict(vd)
-        badv[kz] = 1.0
-        with pytest.raises(AssertionError):
-            ox.check_partition(ex, badv, vb, cs)             # non-zero padding
-
-
-def test_incomplete_plan_raises():
-    rng = np.random.default_rng(2)
-    A = synth.assemble(rng, 50, 50, n_scatter=100)
-    with pytest.raises(ValueError):
-        ox.run_plan(50, 50, A["row"], A["col"], A["val"], [(ox.VDIA, None)])
+def test_prepass_equals_algorithm1_per_box_and_recovers_planted_blocks(seed):
+    # The candidate-region pre-pass is not in the paper.  What it must do:
+    # (1) recover full planted blocks that lie far apart (the ground truth
+    # here, independent of any implementation), and (2) give exactly what
+    # literal Algorithm 1 (tile = 0) gives when run on each candidate box's
+    # submatrix alone.  (Literal Algorithm 1 on the whole matrix can lose a
+    # block to the "row or column already used" rule, so it is not the
+    # reference for the whole matrix.)
+    rng = np.random.default_rng(400 + seed)
+    m = n = 160
+    planted = [(4, 6, 20, 24), (60, 70, 30, 18), (120, 120, 25, 30)]
+    A = synth.assemble(rng, m, n, blocks=[(r0, c0, nr, nc, 1.0) for (r0, c0, nr, nc) in planted], n_scatter=150)
+    p8 = ox.Params(delta=0.5, a_min=300, max_span=64, tile=8)
+    ex = ox.run_plan(m, n, A["row"], A["col"], A["val"], [(ox.VBR, p8), (ox.CSR, None)])
+    assert ex.blocks == sorted((r0, nr, c0, nc) for (r0, c0, nr, nc) in planted)
+    rows, cols, _ = ox.canonicalize(m, n, A["row"], A["col"], A["val"])
+    R = ox.Residual(m, n, rows, cols, np.arange(rows.size))
+    per_box = []
+    p0 = ox.Params(delta=0.5, a_min=300, max_span=64, tile=0, coverage_min=0.0)
+    for (r0, r1, c0, c1) in ox.candidate_regions(R, p8):
+        sel = (rows >= r0) & (rows < r1) & (cols >= c0) & (cols < c1)
+        Rb = ox.Residual(r1 - r0, c1 - c0, rows[sel] - r0, cols[sel] - c0, np.arange(int(sel.sum())))
+        per_box += [(a + r0, b + r0, c + c0, d + c0) for (a, b, c, d, _) in ox.partition_blocks(Rb, p0)]
+    assert sorted((a, b - a, c, d - c) for (a, b, c, d) in per_box) == ex.blocks

@@ -72,11 +72,7 @@ typedef enum { SABLE_FP32 = 0, SABLE_BF16_BLOCKS = 1, SABLE_FP32_SPLIT = 2 } sab
  *   coverage_min share of entries blocks must cover, else none are kept (0.08)
  *   max_span     cap on FindBlock's outer span (Algorithm 2)
  *   tile         candidate-region pre-pass cell size; 0 runs Algorithm 1 on
- *                the whole matrix
- *   device_search 1: FindBlock runs on the current CUDA device for regions of
- *                at least 128 outer lines and at most 4096 inner positions
- *                (same result as the host search); 0 (default): host only.
- *                A CUDA error makes sable_extract return SABLE_ERR_CUDA. */
+ *                the whole matrix */
 typedef struct {
   double delta;
   int64_t a_min;
@@ -87,7 +83,6 @@ typedef struct {
   double coverage_min;
   int32_t max_span;
   int32_t tile;
-  int32_t device_search;
 } sable_extract_params;
 
 /* Summary of an extracted plan.  Byte counts are the algorithmic bytes one
@@ -328,7 +323,10 @@ sable_status sable_batch_destroy(sable_batch_t batch);
  * counted in a hash table over at most 2^22 sampled entries).  The exact
  * definitions are in the implementation's header comment.  `work` is a device
  * workspace of at least sable_features_workspace_bytes(m, n, nnz) bytes.
- * Errors: SABLE_ERR_INVALID; SABLE_ERR_CUDA. */
+ * Indices should lie in [0, m) x [0, n); the kernels check every entry,
+ * skip one that does not (it is never used as an index) and then write every
+ * feature as NaN, since the host cannot see the device arrays before the
+ * asynchronous launch.  Errors: SABLE_ERR_INVALID; SABLE_ERR_CUDA. */
 #define SABLE_NFEAT 24
 int64_t sable_features_workspace_bytes(int64_t m, int64_t n, int64_t nnz);
 sable_status sable_features(int64_t m, int64_t n, int64_t nnz, const int32_t *row, const int32_t *col,
@@ -343,13 +341,16 @@ sable_status sable_features(int64_t m, int64_t n, int64_t nnz, const int32_t *ro
  * cause.  The scratch (row and diagonal counters, the tile hash table) is one
  * fixed array of SABLE_FEATURES_NOALLOC_MAX_BYTES (32 MiB) that every GPU
  * holds from loading the library's device code until the process exits.
- *  - Same inputs, output and results as sable_features; no workspace argument.
+ *  - Same inputs, output and results as sable_features (entries outside the
+ *    matrix included: skipped, every feature NaN); no workspace argument.
  *  - Sizes whose workspace, sable_features_workspace_bytes(m, n, nnz), exceeds
  *    SABLE_FEATURES_NOALLOC_MAX_BYTES are rejected with SABLE_ERR_UNSUPPORTED
  *    before any device work (for example nnz <= 2^20 with 2m + n <= 2,000,000 fits).
  *  - The first call on a device looks up that device's address of the array
  *    (cudaGetSymbolAddress, with the device current); make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the life of the
+ *    process: do not call this entry point after cudaDeviceReset or any other
+ *    teardown of the device's primary context.
  *  - The call allocates nothing: no cudaMalloc, cudaFree or allocating library
  *    routine.  It clears the array's counters and table on `stream` before
  *    using them, since the array keeps the previous call's contents.

@@ -32,8 +32,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sable_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 
 def build() -> str:
@@ -47,22 +49,51 @@ def build() -> str:
     return _SO
 
 
+def build_omp():
+    """The same C file with -fopenmp (the all-cores CPU baseline); None when
+    the host compiler has no OpenMP."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not os.path.exists(_SO_OMP)) or os.path.getmtime(_SO_OMP) < os.path.getmtime(_SRC):
+        tmp = _SO_OMP + f".{os.getpid()}.tmp"
+        r = subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+                            "-fopenmp", _SRC, "-o", tmp], capture_output=True)
+        if r.returncode != 0:
+            return None
+        os.replace(tmp, _SO_OMP)
+    return _SO_OMP
+
+
+def _bind(lib):
+    i64, p = ctypes.c_int64, ctypes.c_void_p
+    lib.oracle_spmv_coo.argtypes = [i64, i64, p, p, p, p, p]
+    lib.oracle_spmv_coo_f32.argtypes = [i64, i64, p, p, p, p, p]
+    lib.oracle_spmm_coo_f32.argtypes = [i64, i64, p, p, p, p, i64, i64, p, i64]
+    lib.oracle_spmm_coo_rows_f32.argtypes = [i64, i64, p, p, p, p, i64, i64, i64, p, p, p]
+    lib.oracle_coo_rows.argtypes = [i64, i64, p, p, p]
+    lib.oracle_spmv_rows_f32.argtypes = [i64, p, p, p, p, p, p]
+    for f in (lib.oracle_spmv_coo, lib.oracle_spmv_coo_f32, lib.oracle_spmm_coo_f32,
+              lib.oracle_spmm_coo_rows_f32, lib.oracle_coo_rows, lib.oracle_spmv_rows_f32):
+        f.restype = None
+    lib.oracle_threads.argtypes = []
+    lib.oracle_threads.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            i64, p = ctypes.c_int64, ctypes.c_void_p
-            lib.oracle_spmv_coo.argtypes = [i64, i64, p, p, p, p, p]
-            lib.oracle_spmv_coo_f32.argtypes = [i64, i64, p, p, p, p, p]
-            lib.oracle_spmm_coo_f32.argtypes = [i64, i64, p, p, p, p, i64, i64, p, i64]
-            lib.oracle_spmm_coo_rows_f32.argtypes = [i64, i64, p, p, p, p, i64, i64,
-                                                     i64, p, p, p]
-            for f in (lib.oracle_spmv_coo, lib.oracle_spmv_coo_f32,
-                      lib.oracle_spmm_coo_f32, lib.oracle_spmm_coo_rows_f32):
-                f.restype = None
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+def _load_omp():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            so = build_omp()
+            _lib_omp = _bind(ctypes.CDLL(so)) if so else False
+    return _lib_omp or None
 
 
 def _ptr(a: np.ndarray) -> int:
@@ -95,6 +126,38 @@ def spmv(m: int, row, col, val, x) -> np.ndarray:
         lib.oracle_spmv_coo_f32(int(m), val.size, _ptr(row), _ptr(col), _ptr(val), _ptr(x),
                                 _ptr(y))
     return y
+
+
+class RowOrder:
+    """The COO triples grouped by row (stable counting sort, input order kept
+    within a row), for the row-loop form of y = A x."""
+
+    def __init__(self, m: int, row, col, val):
+        self.m = int(m)
+        self.row, self.col, self.val = _coo(row, col, val, np.float32)
+        self.rp = np.empty(self.m + 1, dtype=np.int64)
+        self.perm = np.empty(self.row.size, dtype=np.int64)
+        _load().oracle_coo_rows(self.m, self.row.size, _ptr(self.row), self.rp.ctypes.data,
+                                self.perm.ctypes.data)
+
+    def spmv(self, x, threads: bool = False) -> np.ndarray:
+        """y = A x in FP64, one row at a time: identical to ``spmv`` (same
+        terms in the same order per row).  threads=True runs the OpenMP build
+        over the rows on every host core; raises if there is none."""
+        lib = _load_omp() if threads else _load()
+        if lib is None:
+            raise RuntimeError("the C oracle could not be built with OpenMP")
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.empty(self.m, dtype=np.float64)
+        lib.oracle_spmv_rows_f32(self.m, self.rp.ctypes.data, self.perm.ctypes.data, _ptr(self.col),
+                                 _ptr(self.val), _ptr(x), _ptr(y))
+        return y
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP build of the oracle runs (0 if it could not be built)."""
+    lib = _load_omp()
+    return int(lib.oracle_threads()) if lib else 0
 
 
 def spmm(m: int, row, col, val, B) -> np.ndarray:

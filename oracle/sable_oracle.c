@@ -72,3 +72,47 @@ void oracle_spmm_coo_rows_f32(int64_t m, int64_t nnz, const int32_t *row,
     for (int64_t j = 0; j < N; ++j) o[j] += a * (double)b[j];
   }
 }
+
+/* COO -> CSR by a stable counting sort on the row index: rp[0..m] row
+ * pointers, perm[0..nnz) the COO positions in row order, input order kept
+ * within each row.  A CSR row loop over this order adds each row's terms in
+ * the same order as the COO loop above, so its FP64 results are identical. */
+void oracle_coo_rows(int64_t m, int64_t nnz, const int32_t *row, int64_t *rp,
+                     int64_t *perm) {
+  for (int64_t i = 0; i <= m; ++i) rp[i] = 0;
+  for (int64_t k = 0; k < nnz; ++k) ++rp[row[k] + 1];
+  for (int64_t i = 0; i < m; ++i) rp[i + 1] += rp[i];
+  int64_t *at = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
+  if (!at) return;
+  for (int64_t i = 0; i < m; ++i) at[i] = rp[i];
+  for (int64_t k = 0; k < nnz; ++k) perm[at[row[k]]++] = k;
+  free(at);
+}
+
+/* y[0..m) = A x from the row order of oracle_coo_rows: y_i = sum over the
+ * row's terms, FP32 inputs widened per term.  Built twice: plainly, and with
+ * -fopenmp, where the rows are shared among the host's threads (each row
+ * still summed by one thread in the order above); oracle_threads() says how
+ * many threads that build runs. */
+void oracle_spmv_rows_f32(int64_t m, const int64_t *rp, const int64_t *perm,
+                          const int32_t *col, const float *val, const float *x,
+                          double *y) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1024)
+#endif
+  for (int64_t i = 0; i < m; ++i) {
+    double s = 0.0;
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+      const int64_t k = perm[q];
+      s += (double)val[k] * (double)x[col[k]];
+    }
+    y[i] = s;
+  }
+}
+
+#ifdef _OPENMP
+#include <omp.h>
+int oracle_threads(void) { return omp_get_max_threads(); }
+#else
+int oracle_threads(void) { return 1; }
+#endif

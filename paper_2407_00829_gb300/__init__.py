@@ -58,7 +58,7 @@ class Params(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("a_min", ctypes.c_int64), ("l_seg", ctypes.c_int32),
                 ("w_max", ctypes.c_int32), ("d_max", ctypes.c_int64), ("count_min", ctypes.c_int64),
                 ("coverage_min", ctypes.c_double), ("max_span", ctypes.c_int32),
-                ("tile", ctypes.c_int32), ("device_search", ctypes.c_int32)]
+                ("tile", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -59,7 +59,12 @@ inline double score2(int64_t nnz, int64_t a, double delta) {
   return t * t * t / (double)a;
 }
 
-using Best = FindBest;   // half-open ends
+// Best window of a region: score (squared, above), outer [o0, o1), inner
+// [i0, i1) (half-open); sc < 0 = none.
+struct Best {
+  double sc = -1.0;
+  int64_t o0 = 0, o1 = 0, i0 = 0, i1 = 0;
+};
 
 struct Region { int64_t r0, r1, c0, c1; };
 
@@ -310,25 +315,14 @@ struct Partitioner {
   const sable_extract_params &p;
   std::vector<uint8_t> used_r, used_c;
   std::vector<BlockFound> blocks;
-  DeviceLines *dR = nullptr, *dRT = nullptr;   // device copies (device_search)
 
   Partitioner(const Csr &R_, const Csr &RT_, const sable_extract_params &p_)
       : R(R_), RT(RT_), p(p_), used_r(R_.m, 0), used_c(R_.n, 0) {}
-  ~Partitioner() {
-    device_lines_free(dR);
-    device_lines_free(dRT);
-  }
-
-  Best search(const Csr &M, DeviceLines *dM, int64_t O0, int64_t O1, int64_t I0, int64_t I1) {
-    Best b;
-    if (dM && find_block_device(dM, O0, O1, I0, I1, p, isqrt_ceil(p.a_min), b)) return b;
-    return find_block(M, O0, O1, I0, I1, p);
-  }
 
   void decompose(int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
     if ((r1 - r0) * (c1 - c0) < p.a_min) return;
-    Best b = search(R, dR, r0, r1, c0, c1);
-    const Best bt = search(RT, dRT, c0, c1, r0, r1);
+    Best b = find_block(R, r0, r1, c0, c1, p);
+    const Best bt = find_block(RT, c0, c1, r0, r1, p);
     if (bt.sc > b.sc) b = Best{bt.sc, bt.i0, bt.i1, bt.o0, bt.o1};
     if (b.sc < 0) return;
     int64_t br0 = b.o0, br1 = b.o1, bc0 = b.i0, bc1 = b.i1;
@@ -355,10 +349,6 @@ struct Partitioner {
 
 std::vector<BlockFound> partition_blocks(const Csr &R, const Csr &RT, const sable_extract_params &p) {
   Partitioner P(R, RT, p);
-  if (p.device_search) {
-    P.dR = device_lines(R);
-    P.dRT = device_lines(RT);
-  }
   std::vector<Region> regions;
   if (p.tile <= 0) regions.push_back({0, R.m, 0, R.n});
   else regions = candidate_regions(R, p);

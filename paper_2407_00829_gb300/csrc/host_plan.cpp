@@ -76,7 +76,6 @@ void sable_default_params(sable_extractor kind, sable_extract_params *o) {
   o->coverage_min = 0.08;
   o->max_span = 512;
   o->tile = 8;
-  o->device_search = 0;
 }
 
 sable_status sable_plan_create(int64_t m, int64_t n, int64_t nnz, const int32_t *row,
@@ -146,7 +145,7 @@ sable_status sable_plan_add_extractor(sable_plan_t P, sable_extractor kind,
   if (params) p = *params;
   if (!(p.delta > 0.0 && p.delta <= 1.0) || p.a_min < 1 || p.l_seg < 1 || p.w_max < 0 || p.w_max > 512 ||
       p.d_max < 0 || p.count_min < 0 || !(p.coverage_min >= 0.0) || p.max_span < 1 ||
-      p.tile < 0 || (p.device_search != 0 && p.device_search != 1))
+      p.tile < 0)
     return SABLE_ERR_INVALID;
   P->extractors.push_back({kind, p});
   P->stage_regions.emplace_back();
@@ -344,8 +343,6 @@ sable_status sable_extract(sable_plan_t P) {
                    32 * (S.n_segments + S.n_blocks) + 4 * P->n + 4 * P->m;
   } catch (const std::bad_alloc &) {
     return fail(P, SABLE_ERR_OOM);
-  } catch (const std::runtime_error &) {   // a CUDA error of the device search
-    return fail(P, SABLE_ERR_CUDA);
   }
   P->extracted = true;
   return SABLE_OK;

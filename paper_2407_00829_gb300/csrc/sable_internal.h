@@ -175,20 +175,6 @@ struct BlockFound { int64_t r0, r1, c0, c1, nnz; };
 std::vector<BlockFound> partition_blocks(const Csr &R, const Csr &RT, const sable_extract_params &p);
 // threads used by the host extractors
 int host_threads();
-// sable_inspect.cu: FindBlock (Algorithm 2) on the device.  FindBest is the
-// best window of a region: score (squared, see the block extractor), outer
-// [o0, o1), inner [i0, i1); sc < 0 = none.
-struct FindBest {
-  double sc = -1.0;
-  int64_t o0 = 0, o1 = 0, i0 = 0, i1 = 0;
-};
-struct DeviceLines;   // a CSR (or CSC) copy on the device
-DeviceLines *device_lines(const Csr &M);   // throws std::runtime_error on a CUDA error
-void device_lines_free(DeviceLines *D);
-// false when the region is not one the device search takes (too few outer
-// lines, too wide an inner range); throws std::runtime_error on a CUDA error
-bool find_block_device(DeviceLines *D, int64_t O0, int64_t O1, int64_t I0, int64_t I1,
-                       const sable_extract_params &p, int64_t s_min, FindBest &best);
 // sable_tc.cu: BF16 VBR blocks on the tensor cores
 void pack_vbr_bf16(const std::vector<Block> &blks, const std::vector<float> &canon,
                    std::vector<uint16_t> &packed, std::vector<float> &scales, std::vector<int64_t> &offs,

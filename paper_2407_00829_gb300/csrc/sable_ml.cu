@@ -15,6 +15,10 @@
 //          candidate test); tiles are counted in a hash table
 //   23     log2(N + 1)/8, N = dense columns of the product (0 for SpMV), set by
 //          the caller after the call (written 0 here)
+// Entries whose row is outside [0, m) or column outside [0, n) are skipped
+// (never used as an index) and counted; if there is any, every feature is
+// written as NaN.  The final step is FP32, with the row-length variance's
+// numerator m sum L^2 - (sum L)^2 formed exactly in 128-bit integers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,13 +34,19 @@ constexpr int kFeat = 24;
 constexpr int kThreads = 256;
 constexpr unsigned long long kEmpty = 0xffffffffffffffffull;
 
+constexpr int kAccOutside = 21;   // acc slot: entries outside the matrix
+
 __global__ void feat_count(int64_t nnz, const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-                           int64_t m, int32_t *__restrict__ rowlen, int32_t *__restrict__ dcount,
+                           int64_t m, int64_t n, int32_t *__restrict__ rowlen, int32_t *__restrict__ dcount,
                            unsigned long long *__restrict__ keys, int32_t *__restrict__ cnt, int64_t slots,
                            int64_t stride, int64_t ntile_cols, unsigned long long *__restrict__ acc) {
-  unsigned long long near = 0;
+  unsigned long long near = 0, outside = 0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = row[k], j = col[k];
+    if ((uint64_t)i >= (uint64_t)m || (uint64_t)j >= (uint64_t)n) {
+      ++outside;
+      continue;
+    }
     atomicAdd(&rowlen[i], 1);
     atomicAdd(&dcount[j - i + m - 1], 1);
     near += (j - i <= 64 && i - j <= 64);
@@ -54,15 +64,18 @@ __global__ void feat_count(int64_t nnz, const int32_t *__restrict__ row, const i
     }
   }
   atomicAdd(&acc[0], near);
+  if (outside) atomicAdd(&acc[kAccOutside], outside);
 }
 
 __global__ void feat_tiles(int64_t nnz, const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-                           const unsigned long long *__restrict__ keys, const int32_t *__restrict__ cnt,
-                           int64_t slots, int64_t stride, int64_t ntile_cols, unsigned long long *__restrict__ acc) {
+                           int64_t m, int64_t n, const unsigned long long *__restrict__ keys,
+                           const int32_t *__restrict__ cnt, int64_t slots, int64_t stride, int64_t ntile_cols,
+                           unsigned long long *__restrict__ acc) {
   unsigned long long b[4] = {0, 0, 0, 0}, sampled = 0;
   for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * stride; k < nnz;
        k += (int64_t)gridDim.x * blockDim.x * stride) {
     const int64_t i = row[k], j = col[k];
+    if ((uint64_t)i >= (uint64_t)m || (uint64_t)j >= (uint64_t)n) continue;   // counted by feat_count
     const unsigned long long key = (unsigned long long)((i >> 3) * ntile_cols + (j >> 3));
     unsigned long long h = (key * 0x9E3779B97F4A7C15ull) >> 20;
     int c = 0;
@@ -113,20 +126,34 @@ __global__ void feat_reduce(int64_t m, int64_t nd, const int32_t *__restrict__ r
 __global__ void feat_final(int64_t m, int64_t n, int64_t nnz, const unsigned long long *__restrict__ acc,
                            float *__restrict__ out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double M = (double)m, NZ = (double)nnz;
-  const double mean = m > 0 ? (double)acc[14] / M : 0.0;
-  const double var = m > 0 ? fmax(0.0, (double)acc[15] / M - mean * mean) : 0.0;
-  out[0] = (float)(log2(M + 1.0) / 24.0);
-  out[1] = (float)(log2((double)n + 1.0) / 24.0);
-  out[2] = (float)(log2(NZ + 1.0) / 32.0);
-  out[3] = (float)(log2(mean + 1.0) / 8.0);
-  out[4] = (float)((mean > 0 ? sqrt(var) / mean : 0.0) / 8.0);
-  out[5] = (float)(log2((double)acc[16] + 1.0) / 16.0);
-  for (int q = 0; q < 8; ++q) out[6 + q] = m > 0 ? (float)((double)acc[6 + q] / M) : 0.f;
-  for (int q = 0; q < 4; ++q) out[14 + q] = nnz > 0 ? (float)((double)acc[17 + q] / NZ) : 0.f;
-  out[18] = nnz > 0 ? (float)((double)acc[0] / NZ) : 0.f;
-  const double smp = (double)acc[5];
-  for (int q = 0; q < 4; ++q) out[19 + q] = smp > 0 ? (float)((double)acc[1 + q] / smp) : 0.f;
+  if (acc[kAccOutside] != 0) {   // an entry outside the matrix: no feature is meaningful
+    for (int q = 0; q < kFeat; ++q) out[q] = __int_as_float(0x7fc00000);
+    return;
+  }
+  const float M = (float)m, NZ = (float)nnz;
+  const unsigned long long s = acc[14], s2 = acc[15];
+  const float mean = m > 0 ? (float)s / M : 0.f;
+  // coefficient of variation sqrt(var) / mean = sqrt(m s2 - s^2) / s, the
+  // numerator exact: m s2 < 2^94 as a 128-bit product, s^2 < 2^62
+  float cv = 0.f;
+  if (m > 0 && s > 0) {
+    const unsigned long long mu = (unsigned long long)m;
+    const unsigned long long lo1 = mu * s2, hi1 = __umul64hi(mu, s2), sq = s * s;
+    const unsigned long long lo = lo1 - sq, hi = hi1 - (lo1 < sq ? 1ull : 0ull);
+    const float num = (float)hi * 18446744073709551616.0f + (float)lo;
+    cv = sqrtf(num) / (float)s;
+  }
+  out[0] = log2f(M + 1.f) / 24.f;
+  out[1] = log2f((float)n + 1.f) / 24.f;
+  out[2] = log2f(NZ + 1.f) / 32.f;
+  out[3] = log2f(mean + 1.f) / 8.f;
+  out[4] = cv / 8.f;
+  out[5] = log2f((float)acc[16] + 1.f) / 16.f;
+  for (int q = 0; q < 8; ++q) out[6 + q] = m > 0 ? (float)acc[6 + q] / M : 0.f;
+  for (int q = 0; q < 4; ++q) out[14 + q] = nnz > 0 ? (float)acc[17 + q] / NZ : 0.f;
+  out[18] = nnz > 0 ? (float)acc[0] / NZ : 0.f;
+  const float smp = (float)acc[5];
+  for (int q = 0; q < 4; ++q) out[19 + q] = smp > 0.f ? (float)acc[1 + q] / smp : 0.f;
   out[23] = 0.f;
 }
 
@@ -359,8 +386,9 @@ sable_status sable_features(int64_t m, int64_t n, int64_t nnz, const int32_t *ro
   const int64_t ntc = (n + 7) / 8;
   const int grid = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (nnz + kThreads - 1) / kThreads));
   if (nnz > 0) {
-    feat_count<<<grid, kThreads, 0, st>>>(nnz, row, col, m, rowlen, dcount, keys, cnt, w.slots, w.stride, ntc, acc);
-    feat_tiles<<<grid, kThreads, 0, st>>>(nnz, row, col, keys, cnt, w.slots, w.stride, ntc, acc);
+    feat_count<<<grid, kThreads, 0, st>>>(nnz, row, col, m, n, rowlen, dcount, keys, cnt, w.slots, w.stride, ntc,
+                                          acc);
+    feat_tiles<<<grid, kThreads, 0, st>>>(nnz, row, col, m, n, keys, cnt, w.slots, w.stride, ntc, acc);
   }
   const int64_t nd = m + n > 0 ? m + n - 1 : 0;
   const int gridr = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (std::max(m, nd) + kThreads - 1) / kThreads));
@@ -393,8 +421,9 @@ sable_status sable_features_noalloc(int64_t m, int64_t n, int64_t nnz, const int
   const int64_t ntc = (n + 7) / 8;
   const int grid = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (nnz + kThreads - 1) / kThreads));
   if (nnz > 0) {
-    feat_count<<<grid, kThreads, 0, st>>>(nnz, row, col, m, rowlen, dcount, keys, cnt, w.slots, w.stride, ntc, acc);
-    feat_tiles<<<grid, kThreads, 0, st>>>(nnz, row, col, keys, cnt, w.slots, w.stride, ntc, acc);
+    feat_count<<<grid, kThreads, 0, st>>>(nnz, row, col, m, n, rowlen, dcount, keys, cnt, w.slots, w.stride, ntc,
+                                          acc);
+    feat_tiles<<<grid, kThreads, 0, st>>>(nnz, row, col, m, n, keys, cnt, w.slots, w.stride, ntc, acc);
   }
   const int64_t nd = m + n > 0 ? m + n - 1 : 0;
   const int gridr = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (std::max(m, nd) + kThreads - 1) / kThreads));

@@ -72,3 +72,19 @@ def test_training_reduces_loss():
         net.adam(lr=3e-3)
     last = float(net.grad(Xd, Td).item())
     assert last < 0.2 * first
+
+
+def test_features_entry_outside_the_matrix_gives_nan_and_no_stray_write():
+    # one column index past n and one negative row: the kernels skip both
+    # (bounds-checked) and every feature comes back NaN; a valid call
+    # afterwards is exact again
+    A = _mats()[1]
+    row = A["row"].copy()
+    col = A["col"].copy()
+    col[5] = A["n"] + 3
+    row[9] = -1
+    f = sable.features(A["m"], A["n"], torch.from_numpy(row).cuda(), torch.from_numpy(col).cuda()).cpu().numpy()
+    assert np.isnan(f).all()
+    good = sable.features(A["m"], A["n"], torch.from_numpy(A["row"]).cuda(),
+                          torch.from_numpy(A["col"]).cuda()).cpu().numpy()
+    np.testing.assert_allclose(good, ml.features(A["m"], A["n"], A["row"], A["col"]), rtol=1e-5, atol=1e-6)

@@ -415,3 +415,23 @@ def test_prepass_equals_algorithm1_per_box_and_recovers_planted_blocks(seed):
         Rb = ox.Residual(r1 - r0, c1 - c0, rows[sel] - r0, cols[sel] - c0, np.arange(int(sel.sum())))
         per_box += [(a + r0, b + r0, c + c0, d + c0) for (a, b, c, d, _) in ox.partition_blocks(Rb, p0)]
     assert sorted((a, b - a, c, d - c) for (a, b, c, d) in per_box) == ex.blocks
+
+
+@pytest.mark.parametrize("threads", [False, True])
+def test_row_order_spmv_is_identical_to_the_coo_loop(threads):
+    # the row-loop form adds each row's terms in the COO input order, so its
+    # FP64 result is bit-identical to the COO loop, with or without threads
+    rng = np.random.default_rng(21)
+    m, n, nnz = 5000, 3000, 60000
+    row = rng.integers(0, m, nnz).astype(np.int32)
+    col = rng.integers(0, n, nnz).astype(np.int32)
+    val = rng.standard_normal(nnz).astype(np.float32)
+    x = rng.standard_normal(n).astype(np.float32)
+    ref = oracle.spmv(m, row, col, val, x)
+    ro = oracle.RowOrder(m, row, col, val)
+    if threads and oracle.omp_threads() == 0:
+        pytest.skip("no OpenMP in this host compiler")
+    y = ro.spmv(x, threads=threads)
+    assert np.array_equal(y.view(np.uint64), ref.view(np.uint64))
+    assert np.all(np.diff(ro.rp) >= 0) and ro.rp[-1] == nnz
+    assert np.all(np.diff(row[ro.perm].astype(np.int64)) >= 0)      # grouped by row

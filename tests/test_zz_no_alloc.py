@@ -65,3 +65,30 @@ def test_noalloc_matches_workspace_features_on_two_calls():
         ref = sable.features(A["m"], A["n"], row, col).cpu().numpy()
         assert np.isfinite(got).all()
         np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.gpu
+def test_noalloc_entry_outside_the_matrix_then_a_valid_call():
+    # an index outside the matrix is skipped by the kernels' own check (never
+    # used to address the shared array) and turns every feature into NaN;
+    # the next valid call on the same array is exact again
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    A = synth.mixed_matrix(np.random.default_rng(9), 5000, 20.0)
+    f = _noalloc()
+    stream = torch.cuda.current_stream().cuda_stream
+    row = np.ascontiguousarray(A["row"], dtype=np.int32)
+    col = np.ascontiguousarray(A["col"], dtype=np.int32)
+    bad = col.copy()
+    bad[3] = A["n"]
+    for c, expect_nan in ((bad, True), (col, False)):
+        rd, cd = torch.from_numpy(row).cuda(), torch.from_numpy(c).cuda()
+        out = torch.zeros(sable.NFEAT, device="cuda")
+        assert f(A["m"], A["n"], row.size, rd.data_ptr(), cd.data_ptr(), out.data_ptr(), stream) == 0
+        got = out.cpu().numpy()
+        if expect_nan:
+            assert np.isnan(got).all()
+        else:
+            ref = sable.features(A["m"], A["n"], rd, cd).cpu().numpy()
+            np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-6)

@@ -48,6 +48,8 @@ def _args():
     ap.add_argument("--spmv-tiling", default=None, metavar="ROWS,BYTES",
                     help="apply this SpMV tiling after the autotuner runs, in place of its choice "
                          "(a fixed tiling for profiling captures, where the tuner's timings are perturbed)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batch workload: keep the default tiling (a short command to profile)")
     ap.add_argument("--spmm-only", action="store_true",
                     help="only the SpMM workload, default tiling, no tuning (a short command to profile)")
     return ap.parse_args()
@@ -443,14 +445,16 @@ def run_batch(args):
     Cs = [torch.empty(A["m"], N, device=dev) for A in mats]
     # tile shapes of the grouped launch, tuned over the whole batch (graph replay timed)
     from paper_2407_00829_gb300 import tune
-    t0 = time.perf_counter()
-    tv, tv_ms = tune.tune_batch(plans, "spmv", xs, ys, stream=stream)
-    tm, tm_ms = tune.tune_batch(plans, "spmm_bf16", Bs, Cs, N=N, stream=stream)
-    autotune = {"spmv": {"chosen": [tv["spmv_rows"], tv["spmv_bytes"]], "ms_chosen": min(tv_ms.values()),
-                         "ms_default": tv_ms[(512, 48 << 10)]},
-                "spmm_bf16": {"chosen": [tm["spmm_rows"], tm["spmm_elems"]], "ms_chosen": min(tm_ms.values()),
-                              "ms_default": tm_ms[(32, 4096)]},
-                "tune_s": round(time.perf_counter() - t0, 1)}
+    autotune = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        tv, tv_ms = tune.tune_batch(plans, "spmv", xs, ys, stream=stream)
+        tm, tm_ms = tune.tune_batch(plans, "spmm_bf16", Bs, Cs, N=N, stream=stream)
+        autotune = {"spmv": {"chosen": [tv["spmv_rows"], tv["spmv_bytes"]], "ms_chosen": min(tv_ms.values()),
+                             "ms_default": tv_ms[(512, 48 << 10)]},
+                    "spmm_bf16": {"chosen": [tm["spmm_rows"], tm["spmm_elems"]], "ms_chosen": min(tm_ms.values()),
+                                  "ms_default": tm_ms[(32, 4096)]},
+                    "tune_s": round(time.perf_counter() - t0, 1)}
     B = sable.Batch(plans)
     nnz = sum(i["nnz"] for i in infos)
     vbytes = sum(i["spmv_bytes"] for i in infos)
@@ -702,6 +706,13 @@ def main():
         sable.probe_gather(xs[0], gcount, gout, stream)
     g_ms = timed(lambda i: sable.probe_gather(xs[i], gcount, gout, stream), 50)
     gather_peak = gcount / (g_ms * 1e-3) / 1e9
+    # the same random reads as 16-byte bulk copies (TMA unit), which skip the
+    # load path's per-line lookups
+    gstat = torch.zeros(1, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        sable.probe_bulk_gather(xs[0], gcount, gout, gstat, stream)
+    b_ms = timed(lambda i: sable.probe_bulk_gather(xs[i], gcount, gout, gstat, stream), 50)
+    bulk_peak = gcount / (b_ms * 1e-3) / 1e9 if int(gstat.item()) == 0 else None
 
     # end to end: pinned host x -> device, SpMV through the public API, y -> pinned host
     xh = torch.from_numpy(x_np).pin_memory()
@@ -805,7 +816,8 @@ def main():
                         "ceiling measured live with sable_probe_gather (hash indices, same n)",
                 "csr_gathers_per_step": info["nnz_csr"], "peak_gathers_per_s": gather_peak * 1e9,
                 "time_at_peak_us": info["nnz_csr"] / (gather_peak * 1e9) * 1e6,
-                "frac_of_step": (info["nnz_csr"] / (gather_peak * 1e9)) / (ms * 1e-3)},
+                "frac_of_step": (info["nnz_csr"] / (gather_peak * 1e9)) / (ms * 1e-3),
+                "bulk_copy_gathers_per_s": bulk_peak * 1e9 if bulk_peak else None},
             "plain_csr": {"kernel": "library CSR kernel, whole matrix", "ms_per_step": ms_plain,
                           "GB/s_hybrid_bytes": nbytes / (ms_plain * 1e-3) / 1e9,
                           "GB/s_own_bytes": info["csr_spmv_bytes"] / (ms_plain * 1e-3) / 1e9},

@@ -289,10 +289,13 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
  * DEVICE arrays of `count` device pointers (x_i: n_i floats, y_i: m_i floats). */
 sable_status sable_batch_spmv(sable_batch_t batch, const float *const *x, float *const *y, void *stream);
 
-/* C_i := A_i B_i, one launch (two with BF16 blocks).  B and C are DEVICE
- * arrays of device pointers; B_i is n_i x N and C_i is m_i x N, row-major with
- * leading dimension N; when N is a multiple of 4 every B_i and C_i must be
- * 16-byte aligned. */
+/* C_i := A_i B_i, one launch (two with tensor-core blocks).  B and C are
+ * DEVICE arrays of device pointers; B_i is n_i x N and C_i is m_i x N,
+ * row-major with leading dimension N; when N is a multiple of 4 every B_i and
+ * C_i must be 16-byte aligned, when N is even 8-byte aligned.  The rows of all
+ * matrices are split over the warps of one persistent launch (a warp per row,
+ * as in sable_spmm), with the column panel and B rows in flight of the first
+ * plan's tiling (sable_plan_set_spmm_cols / sable_plan_set_spmm_depth). */
 sable_status sable_batch_spmm(sable_batch_t batch, const float *const *B, int64_t N, float *const *C,
                               sable_precision prec, void *stream);
 
@@ -403,6 +406,35 @@ sable_status sable_probe_gather(const float *x, int64_t n, int64_t count, float 
  * N and ld are multiples of 4, ld >= N and B is 16-byte aligned. */
 sable_status sable_probe_row_gather(const float *B, int64_t n, int64_t ld, int32_t N, int64_t count, float *out,
                                     void *stream);
+
+/* Calibration: `count` random 16-byte chunks of x (device, n >= 4 floats,
+ * 16-byte aligned; chunk indices from a fixed hash reduced modulo n / 4)
+ * copied into shared memory by the bulk-copy (TMA) unit, cp.async.bulk
+ * completing on mbarriers, one launch on `stream`.  Timing it gives the rate
+ * of random x reads that bypass the load path's per-line lookups, beside
+ * sable_probe_gather's.  `out` (device, one float) may be written; `status`
+ * (device, one int32) receives 0, or SABLE_ERR_TIMEOUT if a wait ran past
+ * the wait limit (the kernel still waits, bounded, for its copies before it
+ * exits).  No counterpart in the paper.  Errors: SABLE_ERR_INVALID. */
+sable_status sable_probe_bulk_gather(const float *x, int64_t n, int64_t count, float *out, int32_t *status,
+                                     void *stream);
+
+/* The budget, in GPU clock cycles, of every bounded device wait of the
+ * library (the tensor-core kernel's mbarrier waits, the bulk-copy probe),
+ * read at each launch; default 4e9 (about 2 s).  A wait that runs past it
+ * makes its kernel record SABLE_ERR_TIMEOUT, skip its remaining work, wait
+ * (bounded) for its own copies in flight, free what it holds and return; the
+ * CUDA context stays usable.  Process-wide.  No counterpart in the paper.
+ * Errors: SABLE_ERR_INVALID unless 1000 <= cycles <= 2^40. */
+sable_status sable_set_wait_limit(int64_t cycles);
+int64_t sable_get_wait_limit(void);
+
+/* A bounded wait that nothing satisfies (an mbarrier whose one expected
+ * arrival never comes), with the current wait limit: `status` (device, one
+ * int32) receives SABLE_ERR_TIMEOUT once the budget runs out.  For testing
+ * that waits end with a status instead of a hang; nothing else is in flight.
+ * No counterpart in the paper.  Errors: SABLE_ERR_INVALID; SABLE_ERR_CUDA. */
+sable_status sable_probe_wait_limit(int32_t *status, void *stream);
 
 /* Accuracy of a result, reduced on the device in FP64: the error of an FP32
  * result y against an FP64 reference (the oracle's), as the normwise

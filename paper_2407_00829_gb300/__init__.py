@@ -37,7 +37,8 @@ EXPORTED = [
     "sable_plan_add_regions", "sable_plan_get_region_stages", "sable_plan_reset",
     "sable_error_workspace_bytes", "sable_error_norms", "sable_plan_get_tiling", "sable_autotune",
     "sable_autotune_cache_clear", "sable_plan_set_spmm_cols", "sable_plan_update_values",
-    "sable_plan_set_spmm_depth", "sable_plan_device_error",
+    "sable_plan_set_spmm_depth", "sable_plan_device_error", "sable_probe_bulk_gather", "sable_set_wait_limit",
+    "sable_get_wait_limit", "sable_probe_wait_limit",
 ]
 
 NFEAT = 24
@@ -118,6 +119,10 @@ def lib():
             "sable_plan_get_tiling": ([p, p], i32),
             "sable_autotune": ([p, i32, i64, p, p, i32, i32, p, p, p], i32),
             "sable_autotune_cache_clear": ([], i64),
+            "sable_probe_bulk_gather": ([p, i64, i64, p, p, p], i32),
+            "sable_set_wait_limit": ([i64], i32),
+            "sable_get_wait_limit": ([], i64),
+            "sable_probe_wait_limit": ([p, p], i32),
             "sable_plan_set_spmm_cols": ([p, i32], i32),
             "sable_plan_update_values": ([p, p, p], i32),
             "sable_plan_set_spmm_depth": ([p, i32], i32),
@@ -420,6 +425,27 @@ def probe_gather(x, count: int, out, stream=None):
     """Launch the random-gather calibration kernel (see include/sable.h)."""
     _check(lib().sable_probe_gather(_dptr(x), x.numel(), int(count), _dptr(out), _stream_handle(stream)),
            "sable_probe_gather")
+
+
+def probe_bulk_gather(x, count: int, out, status, stream=None):
+    """Launch the bulk-copy random-gather calibration kernel (see include/sable.h);
+    ``status`` is a device int32 tensor of one element."""
+    _check(lib().sable_probe_bulk_gather(_dptr(x), x.numel(), int(count), _dptr(out), _dptr(status),
+                                         _stream_handle(stream)), "sable_probe_bulk_gather")
+
+
+def set_wait_limit(cycles: int):
+    """Budget in GPU clock cycles of every bounded device wait (process-wide)."""
+    _check(lib().sable_set_wait_limit(int(cycles)), "sable_set_wait_limit")
+
+
+def wait_limit() -> int:
+    return int(lib().sable_get_wait_limit())
+
+
+def probe_wait_limit(status, stream=None):
+    """A bounded wait nothing satisfies; ``status`` (device int32) gets the outcome."""
+    _check(lib().sable_probe_wait_limit(_dptr(status), _stream_handle(stream)), "sable_probe_wait_limit")
 
 
 def probe_row_gather(B, count: int, out, stream=None):

@@ -1,12 +1,13 @@
 // Batched SpMV / SpMM over many extracted plans in one grouped launch per op,
 // and CUDA-graph capture of those launches.
 //
-// A batch concatenates the row-tile tables of its plans (each tile carries
-// its matrix index) and keeps a device table of the plans' device
-// descriptors, so one persistent launch covers every region of every matrix
-// (and, for SpMM with BF16 blocks, one more launch covers every block tile on
-// the tensor cores).  The plans must stay alive and uploaded while the batch
-// is used.
+// A batch concatenates the SpMV row-tile tables of its plans (each tile
+// carries its matrix index), numbers the rows of all its matrices one after
+// another for the row-split SpMM, and keeps a device table of the plans'
+// device descriptors, so one persistent launch covers every region of every
+// matrix (and, for SpMM with tensor-core blocks, one more launch covers every
+// block tile on the tensor cores).  The plans must stay alive and uploaded
+// while the batch is used.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +25,10 @@ struct sable_batch_s {
   const DevHybrid *mats = nullptr;
   const DevItem *items_v = nullptr, *items_m = nullptr;
   const int32_t *trip = nullptr;
+  const int32_t *fg = nullptr;         // (matrix, block, row group) triples of the FP32 block kernel
+  int n_fg = 0;
+  const int64_t *row_base = nullptr;   // rows of the matrices before each one (count + 1)
+  int64_t rows = 0;                    // all rows of the batch
   int *err = nullptr;
   int n_v = 0, n_m = 0, n_trip = 0, rows_v = 0, rows_m = 0;
 };
@@ -43,13 +48,23 @@ sable_status batch_spmm_launch(sable_batch_t b, const float *const *B, int64_t N
                                sable_precision prec, cudaStream_t st) {
   if (N < 1 || N > (int64_t)65535 * 32) return SABLE_ERR_INVALID;
   if (prec != SABLE_FP32 && prec != SABLE_BF16_BLOCKS && prec != SABLE_FP32_SPLIT) return SABLE_ERR_INVALID;
-  const bool bf16 = prec != SABLE_FP32 && b->n_trip > 0;   // blocks on the tensor cores
-  if (bf16) {
-    const sable_status s = launch_vbr_tc(b->mats, b->trip, b->n_trip, nullptr, 0, nullptr, 0, B, C, (int)N,
-                                         b->sm_count, b->err, st, prec == SABLE_FP32_SPLIT ? 3 : 1);
+  // column panel and depth from the first plan's tiling
+  const Tiling &T = b->plans.empty() ? Tiling{} : b->plans[0]->tiling;
+  // blocks first (matrices whose blocks share no rows): they store their rows
+  // of C on the tensor cores or, FP32, in groups of rows
+  const bool first = b->n_trip > 0;
+  if (first) {
+    const sable_status s =
+        prec == SABLE_FP32
+            ? launch_vbr_rows(b->mats, b->fg, b->n_fg, nullptr, 0, nullptr, 0, B, C, (int)N, T.spmm_cols,
+                              b->sm_count, st)
+            : launch_vbr_tc(b->mats, b->trip, b->n_trip, nullptr, 0, nullptr, 0, B, C, (int)N, b->sm_count, b->err,
+                            st, prec == SABLE_FP32_SPLIT ? 3 : 1);
     if (s) return s;
   }
-  return launch_spmm_grouped(b->mats, b->items_m, b->n_m, b->rows_m, B, C, (int)N, bf16, b->sm_count, st);
+  // the row-split grouped launch
+  return launch_spmm_rows_grouped(b->mats, b->row_base, (int)b->plans.size(), b->rows, B, C, (int)N, first,
+                                  T.spmm_cols, T.spmm_depth, b->sm_count, st);
 }
 
 sable_status capture(sable_batch_t b, sable_graph_t *out, bool spmm, const float *const *in, int64_t N,
@@ -95,7 +110,8 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
   if (!b) return SABLE_ERR_OOM;
   std::vector<DevHybrid> mats;
   std::vector<DevItem> iv, im;
-  std::vector<int32_t> trip;
+  std::vector<int32_t> trip, fg;
+  std::vector<int64_t> row_base(1, 0);
   try {
     for (int32_t i = 0; i < count; ++i) {
       sable_plan_t P = plans[i];
@@ -118,6 +134,12 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
         trip.push_back(P->h_trip[k + 1]);
         trip.push_back(P->h_trip[k + 2]);
       }
+      for (size_t k = 0; k + 2 < P->h_fg.size(); k += 3) {
+        fg.push_back(i);
+        fg.push_back(P->h_fg[k + 1]);
+        fg.push_back(P->h_fg[k + 2]);
+      }
+      row_base.push_back(row_base.back() + P->m);
       b->rows_v = std::max(b->rows_v, P->dev.spmv.rows_max);
       b->rows_m = std::max(b->rows_m, P->dev.spmm.rows_max);
     }
@@ -127,8 +149,9 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
   }
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t s_err = 256, s_m = al(mats.size() * sizeof(DevHybrid)), s_v = al(iv.size() * sizeof(DevItem)),
-               s_i = al(im.size() * sizeof(DevItem)), s_t = al(trip.size() * sizeof(int32_t));
-  const size_t total = s_err + s_m + s_v + s_i + s_t;
+               s_i = al(im.size() * sizeof(DevItem)), s_t = al(trip.size() * sizeof(int32_t)),
+               s_r = al(row_base.size() * sizeof(int64_t)), s_f = al(fg.size() * sizeof(int32_t));
+  const size_t total = s_err + s_m + s_v + s_i + s_t + s_r + s_f;
   if (cudaMalloc(&b->blob, total) != cudaSuccess) {
     (void)cudaGetLastError();
     delete b;
@@ -144,6 +167,10 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
   b->items_m = reinterpret_cast<const DevItem *>(p);
   p += s_i;
   b->trip = reinterpret_cast<const int32_t *>(p);
+  p += s_t;
+  b->row_base = reinterpret_cast<const int64_t *>(p);
+  p += s_r;
+  b->fg = reinterpret_cast<const int32_t *>(p);
   cudaError_t e = cudaMemset(b->err, 0, s_err);
   if (e == cudaSuccess && !mats.empty())
     e = cudaMemcpy((void *)b->mats, mats.data(), mats.size() * sizeof(DevHybrid), cudaMemcpyHostToDevice);
@@ -153,6 +180,10 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
     e = cudaMemcpy((void *)b->items_m, im.data(), im.size() * sizeof(DevItem), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !trip.empty())
     e = cudaMemcpy((void *)b->trip, trip.data(), trip.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy((void *)b->row_base, row_base.data(), row_base.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !fg.empty())
+    e = cudaMemcpy((void *)b->fg, fg.data(), fg.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     cudaFree(b->blob);
@@ -162,6 +193,8 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
   b->n_v = (int)iv.size();
   b->n_m = (int)im.size();
   b->n_trip = (int)(trip.size() / 3);
+  b->n_fg = (int)(fg.size() / 3);
+  b->rows = row_base.back();
   b->device = dev;
   cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
   *out = b;

@@ -228,16 +228,26 @@ __device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, 
   }
 }
 
-// C[:, n0:n0+NT] of one matrix; V = 4 needs N, ldb, ldc multiples of 4 and
-// 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row pointers.
-// acc += sum over the cnt (1..32) entries held by lanes 0..cnt-1 (value v,
-// column c; the lanes past cnt hold c = 0, a row that always exists) of v x
-// the lane's columns of B row c, U rows of B in flight.  Whole groups of U
-// run unchecked; the last group leaves its missing entries out of the sum by
-// a warp-uniform test.
-template <int V, int U>
+// Row-split SpMM works on lane groups: a group of L lanes (8, 16 or 32) owns
+// one row of C and V columns per lane, so a warp holds 32 / L rows at once
+// and a CTA panel covers L V columns.  Small N (32 or 64 columns at V = 4)
+// uses L = 8 or 16: a warp then keeps 32 / L rows' B-row reads in flight
+// instead of idling three quarters of its lanes on one row.  mask: the
+// group's lanes; shuffles use width L, so lane numbers are group-relative.
+template <int L>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (L == 32) return 0xffffffffu;
+  else return ((1u << L) - 1u) << (((threadIdx.x & 31) / L) * L);
+}
+
+// acc += sum over the cnt (1..L) entries held by the group's lanes 0..cnt-1
+// (value v, column c; the lanes past cnt hold c = 0, a row that always
+// exists) of v x the lane's columns of B row c, U rows of B in flight.  Whole
+// groups of U run unchecked; the last group leaves its missing entries out of
+// the sum by a group-uniform test.
+template <int V, int L, int U>
 __device__ __forceinline__ void rows_chunk(typename VecT<V>::T &acc, float v, int c, int cnt,
-                                           const float *__restrict__ Bl, int ldb, bool lane_ok) {
+                                           const float *__restrict__ Bl, int ldb, bool lane_ok, unsigned mask) {
   using Vt = VecT<V>;
   using T = typename Vt::T;
   int j = 0;
@@ -245,117 +255,260 @@ __device__ __forceinline__ void rows_chunk(typename VecT<V>::T &acc, float v, in
     T bj[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int cu = __shfl_sync(kFull, c, j + u);
+      const int cu = __shfl_sync(mask, c, j + u, L);
       bj[u] = lane_ok ? Vt::load(Bl + (int64_t)cu * ldb) : Vt::zero();
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) Vt::fma(acc, __shfl_sync(kFull, v, j + u), bj[u]);
+    for (int u = 0; u < U; ++u) Vt::fma(acc, __shfl_sync(mask, v, j + u, L), bj[u]);
   }
-  if (j < cnt) {   // j + u <= 31
+  if (j < cnt) {   // source lanes past L wrap inside the group: a held entry or c = 0, left out below
     T bj[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int cu = __shfl_sync(kFull, c, j + u);
+      const int cu = __shfl_sync(mask, c, j + u, L);
       bj[u] = lane_ok ? Vt::load(Bl + (int64_t)cu * ldb) : Vt::zero();
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const float vu = __shfl_sync(kFull, v, j + u);
+      const float vu = __shfl_sync(mask, v, j + u, L);
       if (j + u < cnt) Vt::fma(acc, vu, bj[u]);
     }
   }
 }
 
-// SpMM, row split: warp w of the grid owns rows w, w + W, ... (consecutive rows
-// on the warps of one CTA) and sums each row in registers from one stream of
-// entries: the row's VDIA diagonals (columns r + off_lo + k, values strided by
-// the segment's run length), its FP32 block columns (columns c0 + k, values
-// strided by the block's height), then its CSR entries; it stores the row
-// once.  Neighbouring warps walk neighbouring rows of a segment or block at
-// about the same time, so their B rows and strided values are shared in L1.
-// tc: the blocks were multiplied on the tensor cores, which stored their rows
-// of C; the row adds that stored sum instead of the block's entries.  No
-// shared memory and no barriers (the tiled form's per-tile barriers held its
-// B-row gathers to ~60 % of the device's row-gather rate).  FULL: N is a
-// multiple of the panel width 32 V (no per-lane column test).  GEN: the
-// matrix has VDIA segments, or blocks summed here; without it every covering
-// part is a tensor-core block and the row only tests whether it has one.
-template <int V, int U, bool FULL, bool GEN>
+// The sum of one row of A B over the row's covering parts: its VDIA
+// diagonals (columns r + off_lo + k, values strided by the segment's run
+// length) and its FP32 block columns (columns c0 + k, values strided by the
+// block's height), into acc.  tc: the matrix's blocks were stored first (on
+// the tensor cores, or FP32 in row groups), so a block sets pre (the row adds
+// the stored sum) instead.  own: some segment or block summed here covers the
+// row.  A matrix with neither segments nor blocks has no per-row list
+// (srp == nullptr): nothing covers its rows.  t: the lane within its group.
+template <int V, int L, int U>
+__device__ __forceinline__ void row_parts(const DevHybrid &A, int r, const float *__restrict__ Bl, int ldb,
+                                          bool lane_ok, bool tc, typename VecT<V>::T &acc, bool &pre, bool &own,
+                                          int t, unsigned mask) {
+  const int n = A.n;
+  if (A.srp == nullptr) return;
+  const int q1 = __ldg(A.srp + r + 1);
+  for (int q = __ldg(A.srp + r); q < q1; ++q) {   // the segments and blocks covering the row
+    const int ref = __ldg(A.sref + q);
+    const float *vp;
+    int stride, cb, kb, k1;   // entries kb .. k1 - 1: value vp[k * stride], column cb + k
+    if (ref & 1) {
+      if (tc) {
+        pre = true;
+        continue;
+      }
+      const DevBlk b = A.blks[ref >> 1];
+      vp = A.vbr + b.val_off + (r - b.r0);
+      stride = b.nr;
+      cb = b.c0;
+      kb = 0;
+      k1 = b.nc;
+    } else {
+      const DevSeg sg = A.segs[ref >> 1];
+      vp = A.vdia + sg.val_off + (r - sg.base);
+      stride = sg.ld;
+      cb = r + sg.off_lo;   // columns kept inside [0, n)
+      kb = max(0, -cb);
+      k1 = min(sg.ndiag, n - cb);
+    }
+    own = true;
+    for (; kb < k1; kb += L) {
+      const int k = kb + t;
+      float v = 0.f;
+      int c = 0;
+      if (k < k1) {
+        v = __ldg(vp + (int64_t)k * stride);
+        c = cb + k;
+      }
+      rows_chunk<V, L, U>(acc, v, c, min(L, k1 - kb), Bl, ldb, lane_ok, mask);
+    }
+  }
+}
+
+// acc += the row's CSR remainder entries (values and columns streamed once).
+template <int V, int L, int U>
+__device__ __forceinline__ void row_csr(const DevHybrid &A, int r, const float *__restrict__ Bl, int ldb,
+                                        bool lane_ok, typename VecT<V>::T &acc, int t, unsigned mask) {
+  const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
+  for (int base = p0; base < p1; base += L) {
+    const int p = base + t;
+    float v = 0.f;
+    int c = 0;
+    if (p < p1) {
+      v = __ldcs(A.cv + p);
+      c = __ldcs(A.ci + p);
+    }
+    rows_chunk<V, L, U>(acc, v, c, min(L, p1 - base), Bl, ldb, lane_ok, mask);
+  }
+}
+
+// SpMM, row split: lane group gamma of the grid owns rows gamma, gamma + G, ...
+// (consecutive rows on the groups of a warp and the warps of a CTA) and sums
+// each row in registers from one stream of entries: the row's covering parts
+// (row_parts), then its CSR entries; it stores the row once.  Neighbouring
+// groups walk neighbouring rows of a segment or block at about the same time,
+// so their B rows and strided values are shared in L1.  tc: the blocks'
+// rows of C were stored first (tensor cores, or FP32 row groups); the row
+// adds that stored sum instead of the block's entries.  No shared memory and
+// no barriers (the tiled form's per-tile barriers held its B-row gathers to
+// ~60 % of the device's row-gather rate).  FULL: N is a multiple of the panel
+// width L V (no per-lane column test).  GEN: the matrix has VDIA segments, or
+// blocks summed here; without it every covering part is a stored block and
+// the row only tests whether it has one.
+template <int V, int L, int U, bool FULL, bool GEN>
 __global__ void __launch_bounds__(256, U == 8 ? 4 : 5)
 spmm_rows_kernel(const __grid_constant__ DevHybrid A, const float *__restrict__ B, int ldb,
                  float *__restrict__ C, int ldc, int N, int tc) {
   using Vt = VecT<V>;
   using T = typename Vt::T;
-  const int lane = threadIdx.x & 31;
-  const int n0 = blockIdx.y * 32 * V;
-  const int lc = V * lane;
+  constexpr int G = 32 / L;
+  const int t = (threadIdx.x & 31) % L;
+  const unsigned mask = group_mask<L>();
+  const int n0 = blockIdx.y * L * V;
+  const int lc = V * t;
   const bool lane_ok = FULL || n0 + lc < N;
   const float *Bl = B + n0 + lc;
-  const int n = A.n;
-  const int W = gridDim.x * (blockDim.x >> 5);
-  for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < A.m; r += W) {
+  const int W = gridDim.x * (blockDim.x >> 5) * G;
+  for (int r = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * G + (threadIdx.x & 31) / L; r < A.m;
+       r += W) {
     T acc = Vt::zero();
-    bool pre = false;   // C holds the row's tensor-core sum
+    bool pre = false;   // C holds the row's stored block sum
     if constexpr (GEN) {
       bool own = false;
-      const int q1 = __ldg(A.srp + r + 1);
-      for (int q = __ldg(A.srp + r); q < q1; ++q) {   // the segments and blocks covering the row
-        const int ref = __ldg(A.sref + q);
-        const float *vp;
-        int stride, cb, kb, k1;   // entries kb .. k1 - 1: value vp[k * stride], column cb + k
-        if (ref & 1) {
-          if (tc) {
-            pre = true;
-            continue;
-          }
-          const DevBlk b = A.blks[ref >> 1];
-          vp = A.vbr + b.val_off + (r - b.r0);
-          stride = b.nr;
-          cb = b.c0;
-          kb = 0;
-          k1 = b.nc;
-        } else {
-          const DevSeg sg = A.segs[ref >> 1];
-          vp = A.vdia + sg.val_off + (r - sg.base);
-          stride = sg.ld;
-          cb = r + sg.off_lo;   // columns kept inside [0, n)
-          kb = max(0, -cb);
-          k1 = min(sg.ndiag, n - cb);
-        }
-        own = true;
-        for (; kb < k1; kb += 32) {
-          const int k = kb + lane;
-          float v = 0.f;
-          int c = 0;
-          if (k < k1) {
-            v = __ldg(vp + (int64_t)k * stride);
-            c = cb + k;
-          }
-          rows_chunk<V, U>(acc, v, c, min(32, k1 - kb), Bl, ldb, lane_ok);
-        }
-      }
-      if (pre && !own && __ldg(A.rp + r) == __ldg(A.rp + r + 1)) continue;   // stored whole by the tensor cores
+      row_parts<V, L, U>(A, r, Bl, ldb, lane_ok, tc != 0, acc, pre, own, t, mask);
+      if (pre && !own && __ldg(A.rp + r) == __ldg(A.rp + r + 1)) continue;   // stored whole already
     } else {
-      // every covering part is a tensor-core block: a row with one and no
-      // CSR entries is already stored whole
+      // every covering part is a stored block: a row with one and no CSR
+      // entries is already stored whole
       if (A.srp != nullptr && __ldg(A.srp + r) < __ldg(A.srp + r + 1) && __ldg(A.rp + r) == __ldg(A.rp + r + 1))
         continue;
     }
-    const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
-    for (int base = p0; base < p1; base += 32) {
-      const int p = base + lane;
-      float v = 0.f;
-      int c = 0;
-      if (p < p1) {
-        v = __ldcs(A.cv + p);
-        c = __ldcs(A.ci + p);
-      }
-      rows_chunk<V, U>(acc, v, c, min(32, p1 - base), Bl, ldb, lane_ok);
-    }
+    row_csr<V, L, U>(A, r, Bl, ldb, lane_ok, acc, t, mask);
     if (lane_ok) {
       float *dst = C + (int64_t)r * ldc + n0 + lc;
       if constexpr (!GEN) pre = A.srp != nullptr && __ldg(A.srp + r) < __ldg(A.srp + r + 1);
       if (pre) Vt::fma(acc, 1.0f, Vt::load_once(dst));   // exact add of the stored block sum
+      Vt::store_once(dst, acc);
+    }
+  }
+}
+
+// FP32 VBR blocks of SpMM, a group of kGroupRows consecutive rows of one block
+// per lane group: each B row c0 + c that the group needs is loaded once and
+// multiplied by the group's kGroupRows values of block column c, so a block
+// cell costs 1 / kGroupRows of a B-row read instead of one.  Four block
+// columns per step: their 8 x 4 values (column-major, Appendix B: each
+// column's 8 rows consecutive in memory) arrive in one coalesced load per
+// lane (32 / L registers) and reach every lane of the group by shuffles; the
+// next step's values and B rows are loaded before this step's products.  The
+// group's rows of C are stored; the row-split launch then adds each row's
+// other parts to that stored sum, as after the tensor cores.  Work items:
+// (matrix, block, group) triples; Bs / Cs per matrix (leading dimension N) or
+// B0 / C0 for a single matrix.  Only matrices whose blocks share no rows.
+constexpr int kGroupRows = 8;
+
+template <int V, int L, bool FULL>
+__global__ void __launch_bounds__(256, 2)
+vbr_rows_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ trip, int n_items,
+                const float *__restrict__ B0, int ldb0, float *__restrict__ C0, int ldc0,
+                const float *const *__restrict__ Bs, float *const *__restrict__ Cs, int N) {
+  using Vt = VecT<V>;
+  using T = typename Vt::T;
+  constexpr int G = 32 / L, R = 32 / L;   // groups per warp; value registers per lane per step
+  const int t = (threadIdx.x & 31) % L;
+  const unsigned mask = group_mask<L>();
+  const int n0 = blockIdx.y * L * V;
+  const int lc = V * t;
+  const bool lane_ok = FULL || n0 + lc < N;
+  const int W = gridDim.x * (blockDim.x >> 5) * G;
+  for (int it = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * G + (threadIdx.x & 31) / L; it < n_items;
+       it += W) {
+    const int mat = __ldg(trip + 3 * it), bi = __ldg(trip + 3 * it + 1), g = __ldg(trip + 3 * it + 2);
+    const DevHybrid &A = mats[mat];
+    const DevBlk b = A.blks[bi];
+    const float *B = Bs ? Bs[mat] : B0;
+    float *C = Cs ? Cs[mat] : C0;
+    const int ldb = Bs ? N : ldb0, ldc = Cs ? N : ldc0;
+    const int rr0 = g * kGroupRows, nrow = min(kGroupRows, b.nr - rr0);   // 1 .. kGroupRows rows
+    const float *ap = A.vbr + b.val_off + rr0;                           // value (rr0 + j, c) at ap[c nr + j]
+    const float *bp = B + (int64_t)b.c0 * ldb + n0 + lc;
+    // value q = 8 u + j of a step (row j, column c + u) is held by lane q % L, register q / L
+    auto load_step = [&](int c, float (&w)[R], T (&bv)[4]) {
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        const int q = s * L + t, u = q >> 3, j = q & 7;
+        w[s] = (j < nrow && c + u < b.nc) ? __ldg(ap + (int64_t)(c + u) * b.nr + j) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        bv[u] = (lane_ok && c + u < b.nc) ? Vt::load(bp + (int64_t)(c + u) * ldb) : Vt::zero();
+    };
+    T acc[kGroupRows];
+#pragma unroll
+    for (int j = 0; j < kGroupRows; ++j) acc[j] = Vt::zero();
+    float w[R], wn[R];
+    T bv[4], bn[4];
+    load_step(0, w, bv);
+    for (int c = 0; c < b.nc; c += 4) {
+      if (c + 4 < b.nc) load_step(c + 4, wn, bn);   // next step in flight during this one
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < kGroupRows; ++j) {
+          const int q = 8 * u + j;
+          Vt::fma(acc[j], __shfl_sync(mask, w[q / L], q % L, L), bv[u]);
+        }
+#pragma unroll
+      for (int s = 0; s < R; ++s) w[s] = wn[s];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) bv[u] = bn[u];
+    }
+    if (lane_ok) {
+#pragma unroll
+      for (int j = 0; j < kGroupRows; ++j)
+        if (j < nrow) Vt::store_once(C + (int64_t)(b.r0 + rr0 + j) * ldc + n0 + lc, acc[j]);
+    }
+  }
+}
+
+// Many matrices in one row-split launch: the rows of every matrix numbered one
+// after another (row_base[i] = rows of the matrices before i, row_base[count]
+// = all rows); B_i is n_i x N and C_i is m_i x N, leading dimension N.  A
+// group's rows only grow, so the matrix it looks up only moves forward.
+// vbrc: the block launch stored the block rows of every matrix whose blocks
+// share no rows (n_tc > 0); other matrices sum their blocks here.
+template <int V, int L, int U, bool FULL>
+__global__ void __launch_bounds__(256, U == 8 ? 4 : 5)
+spmm_rows_grouped_kernel(const DevHybrid *__restrict__ mats, const int64_t *__restrict__ row_base, int count,
+                         const float *const *__restrict__ Bs, float *const *__restrict__ Cs, int N, int vbrc) {
+  using Vt = VecT<V>;
+  using T = typename Vt::T;
+  constexpr int G = 32 / L;
+  const int t = (threadIdx.x & 31) % L;
+  const unsigned mask = group_mask<L>();
+  const int n0 = blockIdx.y * L * V;
+  const int lc = V * t;
+  const bool lane_ok = FULL || n0 + lc < N;
+  const int64_t total = row_base[count];
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5) * G;
+  int mat = 0;
+  for (int64_t gr = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * G + (threadIdx.x & 31) / L;
+       gr < total; gr += W) {
+    while (row_base[mat + 1] <= gr) ++mat;   // gr < total = row_base[count], so mat < count
+    const DevHybrid &A = mats[mat];
+    const int r = (int)(gr - row_base[mat]);
+    const float *Bl = Bs[mat] + n0 + lc;
+    T acc = Vt::zero();
+    bool pre = false, own = false;
+    row_parts<V, L, U>(A, r, Bl, N, lane_ok, vbrc != 0 && A.n_tc > 0, acc, pre, own, t, mask);
+    if (pre && !own && __ldg(A.rp + r) == __ldg(A.rp + r + 1)) continue;   // stored whole already
+    row_csr<V, L, U>(A, r, Bl, N, lane_ok, acc, t, mask);
+    if (lane_ok) {
+      float *dst = Cs[mat] + (int64_t)r * N + n0 + lc;
+      if (pre) Vt::fma(acc, 1.0f, Vt::load_once(dst));
       Vt::store_once(dst, acc);
     }
   }
@@ -474,7 +627,7 @@ struct Staging {
   std::vector<DevSeg> segs;
   std::vector<float> vdia;
   std::vector<DevBlk> blks;
-  std::vector<int32_t> rp, ci, prp, pci, tc_pairs;
+  std::vector<int32_t> rp, ci, prp, pci, tc_pairs, fg_pairs;
   std::vector<uint16_t> vbr_bf16, vbr_bf16_mid, vbr_bf16_lo;
   std::vector<float> vbr_scale;
   std::vector<float> cv, pcv;
@@ -557,7 +710,11 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
         shared_rows = shared_rows || b.r0 < end;
         end = std::max(end, b.r0 + b.nr);
       }
-      if (!shared_rows) vbr_tc_pairs(H.blks, 0, S->tc_pairs);
+      S->fg_pairs.clear();
+      if (!shared_rows) {
+        vbr_tc_pairs(H.blks, 0, S->tc_pairs);
+        vbr_group_pairs(H.blks, 0, S->fg_pairs);
+      }
     }
     if (!H.segs.empty() || !H.blks.empty()) {   // per row: the segments and blocks covering it
       S->srp.assign(P->m + 1, 0);
@@ -608,6 +765,7 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   const size_t o_bf16_lo = ar.add(S->vbr_bf16_lo.data(), vec_bytes(S->vbr_bf16_lo));
   const size_t o_scale = ar.add(S->vbr_scale.data(), vec_bytes(S->vbr_scale));
   const size_t o_pairs = ar.add(S->tc_pairs.data(), vec_bytes(S->tc_pairs));
+  const size_t o_fg = ar.add(S->fg_pairs.data(), vec_bytes(S->fg_pairs));
   const size_t o_self = ar.reserve(sizeof(DevHybrid));
   const size_t o_rp = ar.add(S->rp.data(), vec_bytes(S->rp));
   const size_t o_ci = ar.add(S->ci.data(), vec_bytes(S->ci));
@@ -668,6 +826,8 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   D.vbr_scale = reinterpret_cast<const float *>(blob + o_scale);
   D.n_tc = (int32_t)(S->tc_pairs.size() / 3);
   P->dev_trip = reinterpret_cast<const int32_t *>(blob + o_pairs);
+  D.n_fg = (int32_t)(S->fg_pairs.size() / 3);
+  P->dev_fg = reinterpret_cast<const int32_t *>(blob + o_fg);
   P->dev_self = reinterpret_cast<DevHybrid *>(blob + o_self);
   D.rp = reinterpret_cast<const int32_t *>(blob + o_rp);
   D.ci = reinterpret_cast<const int32_t *>(blob + o_ci);
@@ -693,6 +853,7 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   P->h_items_v = S->it_v.items;
   P->h_items_m = S->it_m.items;
   P->h_trip = S->tc_pairs;
+  P->h_fg = S->fg_pairs;
   P->h_segs = S->segs;
   P->o_vdia = o_vdia;
   P->o_vbr = o_vbr;
@@ -733,6 +894,25 @@ int grid_for(K kernel, int threads, size_t smem, int items, int sm_count) {
   return std::max(1, std::min(items, g));
 }
 
+}  // namespace
+
+namespace sable {
+// Column panel of the row-split SpMM kernels: V columns per lane and L lanes
+// per row (panel width L V).  cols is the tiling knob (0 = widest the
+// operands allow, 32, 64 or 128 columns); vec: N, the leading dimensions and
+// the operands allow float4 lanes (16-byte aligned), vec2 float2 lanes.
+Panel spmm_panel(int cols, int64_t N, bool vec, bool vec2) {
+  if (vec) {
+    const int L = cols == 32 ? 8 : cols == 64 ? 16 : cols == 128 ? 32 : N <= 32 ? 8 : N <= 64 ? 16 : 32;
+    return {4, L};
+  }
+  if (vec2 && cols != 32) return {2, 32};
+  return {1, 32};
+}
+}  // namespace sable
+
+namespace {
+
 sable_status check_ready(sable_plan_t P) {
   if (!P) return SABLE_ERR_INVALID;
   if (P->sticky) return P->sticky;
@@ -743,13 +923,14 @@ sable_status check_ready(sable_plan_t P) {
   return SABLE_OK;
 }
 
-template <int V, int U>
-void launch_rows(const DevHybrid &D, const float *B, int64_t ldb, float *C, int64_t ldc, int N, int gy, int sms,
-                 bool tc, cudaStream_t st) {
-  const bool full = N % (32 * V) == 0, gen = D.n_segs > 0 || (D.n_blks > 0 && !tc);
-  auto k = gen ? (full ? spmm_rows_kernel<V, U, true, true> : spmm_rows_kernel<V, U, false, true>)
-               : (full ? spmm_rows_kernel<V, U, true, false> : spmm_rows_kernel<V, U, false, false>);
-  dim3 grid(grid_for(k, 256, 0, (D.m + 7) / 8, sms), gy);
+template <int V, int L, int U>
+void launch_rows(const DevHybrid &D, const float *B, int64_t ldb, float *C, int64_t ldc, int N, int sms, bool tc,
+                 cudaStream_t st) {
+  const bool full = N % (L * V) == 0, gen = D.n_segs > 0 || (D.n_blks > 0 && !tc);
+  auto k = gen ? (full ? spmm_rows_kernel<V, L, U, true, true> : spmm_rows_kernel<V, L, U, false, true>)
+               : (full ? spmm_rows_kernel<V, L, U, true, false> : spmm_rows_kernel<V, L, U, false, false>);
+  const int gy = (N + L * V - 1) / (L * V);
+  dim3 grid(grid_for(k, 256, 0, (D.m + 8 * (32 / L) - 1) / (8 * (32 / L)), sms), gy);
   k<<<grid, 256, 0, st>>>(D, B, (int)ldb, C, (int)ldc, N, tc ? 1 : 0);
 }
 
@@ -765,17 +946,25 @@ sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int
                    ((uintptr_t)B & 15) == 0 && ((uintptr_t)C & 15) == 0;
   const bool vec2 = N % 2 == 0 && ldb % 2 == 0 && ldc % 2 == 0 &&
                     ((uintptr_t)B & 7) == 0 && ((uintptr_t)C & 7) == 0;
-  // column panel per CTA: 128 (float4 lanes), 64 (float2) or 32
-  const int cols = P->tiling.spmm_cols;
-  const int V = cols == 32 ? 1 : cols == 64 ? (vec2 ? 2 : 1) : (vec ? 4 : 1);
-  const int gy = (int)((N + 32 * V - 1) / (32 * V));
+  // column panel per CTA: 128, 64 or 32 columns (float4 lanes, 32, 16 or 8
+  // lanes per row), or float2 / scalar lanes when the operands are not aligned
+  const Panel pn = spmm_panel(P->tiling.spmm_cols, N, vec, vec2);
   const int sms = P->sm_count;
-  const bool deep = P->tiling.spmm_depth == 8;   // 8 B rows in flight per warp
-  if (V == 4 && deep) launch_rows<4, 8>(D, B, ldb, C, ldc, (int)N, gy, sms, vbrc, st);
-  else if (V == 4) launch_rows<4, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, vbrc, st);
-  else if (V == 2 && deep) launch_rows<2, 8>(D, B, ldb, C, ldc, (int)N, gy, sms, vbrc, st);
-  else if (V == 2) launch_rows<2, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, vbrc, st);
-  else launch_rows<1, 4>(D, B, ldb, C, ldc, (int)N, gy, sms, vbrc, st);
+  const bool deep = P->tiling.spmm_depth == 8;   // 8 B rows in flight per lane group
+  const int n = (int)N;
+  if (pn.V == 4) {
+    if (pn.L == 8) deep ? launch_rows<4, 8, 8>(D, B, ldb, C, ldc, n, sms, vbrc, st)
+                        : launch_rows<4, 8, 4>(D, B, ldb, C, ldc, n, sms, vbrc, st);
+    else if (pn.L == 16) deep ? launch_rows<4, 16, 8>(D, B, ldb, C, ldc, n, sms, vbrc, st)
+                              : launch_rows<4, 16, 4>(D, B, ldb, C, ldc, n, sms, vbrc, st);
+    else deep ? launch_rows<4, 32, 8>(D, B, ldb, C, ldc, n, sms, vbrc, st)
+              : launch_rows<4, 32, 4>(D, B, ldb, C, ldc, n, sms, vbrc, st);
+  } else if (pn.V == 2) {
+    deep ? launch_rows<2, 32, 8>(D, B, ldb, C, ldc, n, sms, vbrc, st)
+         : launch_rows<2, 32, 4>(D, B, ldb, C, ldc, n, sms, vbrc, st);
+  } else {
+    launch_rows<1, 32, 4>(D, B, ldb, C, ldc, n, sms, vbrc, st);
+  }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SABLE_OK : cuda_fail(P, e);
 }
@@ -801,15 +990,21 @@ sable_status sable_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, 
   const sable_status s = check_ready(P);
   if (s) return s;
   if (prec != SABLE_FP32 && prec != SABLE_BF16_BLOCKS && prec != SABLE_FP32_SPLIT) return SABLE_ERR_INVALID;
-  const bool bf16 = prec != SABLE_FP32 && P->dev.n_tc > 0;   // blocks on the tensor cores
-  if (bf16) {
-    if (N < 1 || ldb < N || ldc < N || !B || !C || N > INT32_MAX) return SABLE_ERR_INVALID;
-    const sable_status s2 = launch_vbr_tc(P->dev_self, P->dev_trip, P->dev.n_tc, B, ldb, C, ldc, nullptr, nullptr,
-                                          (int)N, P->sm_count, P->dev.err, (cudaStream_t)stream,
-                                          prec == SABLE_FP32_SPLIT ? 3 : 1);
+  // blocks first, storing their rows of C: on the tensor cores, or FP32 in
+  // groups of rows; the row-split launch adds the other parts
+  const bool first = P->dev.n_tc > 0;
+  if (first) {
+    if (N < 1 || ldb < N || ldc < N || !B || !C || N > (int64_t)65535 * 32 || ldb > INT32_MAX || ldc > INT32_MAX)
+      return SABLE_ERR_INVALID;
+    const sable_status s2 =
+        prec == SABLE_FP32
+            ? launch_vbr_rows(P->dev_self, P->dev_fg, P->dev.n_fg, B, ldb, C, ldc, nullptr, nullptr, (int)N,
+                              P->tiling.spmm_cols, P->sm_count, (cudaStream_t)stream)
+            : launch_vbr_tc(P->dev_self, P->dev_trip, P->dev.n_tc, B, ldb, C, ldc, nullptr, nullptr, (int)N,
+                            P->sm_count, P->dev.err, (cudaStream_t)stream, prec == SABLE_FP32_SPLIT ? 3 : 1);
     if (s2) return fail(P, s2);
   }
-  return launch_spmm(P, P->dev, B, N, ldb, C, ldc, bf16, (cudaStream_t)stream);
+  return launch_spmm(P, P->dev, B, N, ldb, C, ldc, first, (cudaStream_t)stream);
 }
 
 sable_status sable_csr_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, float *C, int64_t ldc,
@@ -908,10 +1103,12 @@ sable_status sable_plan_reset(sable_plan_t P) {
   P->dev_plain = DevHybrid{};
   P->dev_self = nullptr;
   P->dev_trip = nullptr;
+  P->dev_fg = nullptr;
   P->dev_err = nullptr;
   P->h_items_v.clear();
   P->h_items_m.clear();
   P->h_trip.clear();
+  P->h_fg.clear();
   P->extractors.clear();
   P->stage_regions.clear();
   P->stage_fixed.clear();
@@ -946,6 +1143,78 @@ sable_status sable_plan_destroy(sable_plan_t P) {
 }  // extern "C"
 
 namespace sable {
+
+void vbr_group_pairs(const std::vector<Block> &blks, int32_t mat, std::vector<int32_t> &trip) {
+  for (size_t bi = 0; bi < blks.size(); ++bi)
+    for (int64_t g = 0; g * kGroupRows < blks[bi].nr; ++g) {
+      trip.push_back(mat);
+      trip.push_back((int32_t)bi);
+      trip.push_back((int32_t)g);
+    }
+}
+
+sable_status launch_vbr_rows(const DevHybrid *mats, const int32_t *trip, int n_items, const float *B, int64_t ldb,
+                             float *C, int64_t ldc, const float *const *Bs, float *const *Cs, int N, int cols,
+                             int sm_count, cudaStream_t_ st) {
+  if (n_items == 0) return SABLE_OK;
+  if (N < 1 || N > 65535 * 32) return SABLE_ERR_INVALID;
+  // float4 lanes need N, ldb, ldc multiples of 4 and 16-byte aligned B, C
+  // (batches: every B_i, C_i, documented); float2 lanes even sizes, 8 bytes
+  const bool one = Bs == nullptr;
+  const bool vec4 = N % 4 == 0 && (!one || (ldb % 4 == 0 && ldc % 4 == 0 && ((uintptr_t)B & 15) == 0 &&
+                                             ((uintptr_t)C & 15) == 0));
+  const bool vec2 = N % 2 == 0 && (!one || (ldb % 2 == 0 && ldc % 2 == 0 && ((uintptr_t)B & 7) == 0 &&
+                                             ((uintptr_t)C & 7) == 0));
+  const Panel pn = spmm_panel(cols, N, vec4, vec2);
+  const int gy = (N + pn.L * pn.V - 1) / (pn.L * pn.V);
+  const bool full = N % (pn.L * pn.V) == 0;
+  const int per = 8 * (32 / pn.L);   // items one CTA takes at once
+  auto go = [&](auto k) {
+    dim3 grid(grid_for(k, 256, 0, (n_items + per - 1) / per, sm_count), gy);
+    k<<<grid, 256, 0, st>>>(mats, trip, n_items, B, (int)ldb, C, (int)ldc, Bs, Cs, N);
+  };
+  if (pn.V == 4 && pn.L == 8) full ? go(vbr_rows_kernel<4, 8, true>) : go(vbr_rows_kernel<4, 8, false>);
+  else if (pn.V == 4 && pn.L == 16) full ? go(vbr_rows_kernel<4, 16, true>) : go(vbr_rows_kernel<4, 16, false>);
+  else if (pn.V == 4) full ? go(vbr_rows_kernel<4, 32, true>) : go(vbr_rows_kernel<4, 32, false>);
+  else if (pn.V == 2) full ? go(vbr_rows_kernel<2, 32, true>) : go(vbr_rows_kernel<2, 32, false>);
+  else full ? go(vbr_rows_kernel<1, 32, true>) : go(vbr_rows_kernel<1, 32, false>);
+  if (cudaGetLastError() != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SABLE_ERR_CUDA;
+  }
+  return SABLE_OK;
+}
+
+sable_status launch_spmm_rows_grouped(const DevHybrid *mats, const int64_t *row_base, int count, int64_t rows,
+                                      const float *const *Bs, float *const *Cs, int N, bool vbrc, int cols, int depth,
+                                      int sm_count, cudaStream_t_ st) {
+  if (count == 0 || rows == 0) return SABLE_OK;
+  if (N < 1 || N > 65535 * 32) return SABLE_ERR_INVALID;
+  // B_i, C_i are 16-byte aligned when N is a multiple of 4 (documented), 8-byte when even
+  const Panel pn = spmm_panel(cols, N, N % 4 == 0, N % 2 == 0);
+  const int gy = (N + pn.L * pn.V - 1) / (pn.L * pn.V);
+  const bool deep = depth == 8;
+  const int64_t per = 8 * (32 / pn.L);   // rows one CTA takes at once
+  auto go = [&](auto k) {
+    dim3 grid(grid_for(k, 256, 0, (int)std::min<int64_t>(INT32_MAX, (rows + per - 1) / per), sm_count), gy);
+    k<<<grid, 256, 0, st>>>(mats, row_base, count, Bs, Cs, N, vbrc ? 1 : 0);
+  };
+  const bool full = N % (pn.L * pn.V) == 0;
+#define SABLE_GROUPED(V_, L_)                                                                             \
+  (deep ? (full ? go(spmm_rows_grouped_kernel<V_, L_, 8, true>) : go(spmm_rows_grouped_kernel<V_, L_, 8, false>)) \
+        : (full ? go(spmm_rows_grouped_kernel<V_, L_, 4, true>) : go(spmm_rows_grouped_kernel<V_, L_, 4, false>)))
+  if (pn.V == 4 && pn.L == 8) SABLE_GROUPED(4, 8);
+  else if (pn.V == 4 && pn.L == 16) SABLE_GROUPED(4, 16);
+  else if (pn.V == 4) SABLE_GROUPED(4, 32);
+  else if (pn.V == 2) SABLE_GROUPED(2, 32);
+  else SABLE_GROUPED(1, 32);
+#undef SABLE_GROUPED
+  if (cudaGetLastError() != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SABLE_ERR_CUDA;
+  }
+  return SABLE_OK;
+}
 
 sable_status launch_spmm_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,
                                  const float *const *Bs, float *const *Cs, int N, bool vbrc, int sm_count,

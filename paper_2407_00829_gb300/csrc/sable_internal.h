@@ -86,6 +86,7 @@ struct DevHybrid {
   const uint16_t *vbr_bf16_lo = nullptr;
   const float *vbr_scale = nullptr;  // per block power-of-two scale
   int32_t n_tc = 0;                  // (block, 128-row tile) pairs for the tensor-core path
+  int32_t n_fg = 0;                  // (block, row group) pairs for the FP32 block kernel
   int32_t n_segs = 0, n_blks = 0;
   // per row, the VDIA segments and VBR blocks covering it: refs srp[r] ..
   // srp[r + 1] - 1 of sref, each (index << 1) | (1 for a block); null when
@@ -154,8 +155,9 @@ struct sable_plan_s {
   sable::DevHybrid dev;                // hybrid tables
   sable::DevHybrid *dev_self = nullptr;// device copy of `dev` (matrix table of one entry)
   const int32_t *dev_trip = nullptr;   // (0, block, row tile) triples for the tensor-core path
+  const int32_t *dev_fg = nullptr;     // (0, block, row group) triples for the FP32 block kernel
   std::vector<sable::DevItem> h_items_v, h_items_m;   // host copies of the tile tables
-  std::vector<int32_t> h_trip;
+  std::vector<int32_t> h_trip, h_fg;
   sable::DevHybrid dev_plain;          // whole matrix as CSR (comparison kernel)
   int32_t *dev_err = nullptr;
   int device = -1;
@@ -180,11 +182,23 @@ void pack_vbr_bf16(const std::vector<Block> &blks, const std::vector<float> &can
                    std::vector<uint16_t> &packed, std::vector<float> &scales, std::vector<int64_t> &offs,
                    std::vector<uint16_t> *mid = nullptr, std::vector<uint16_t> *lo = nullptr);
 void vbr_tc_pairs(const std::vector<Block> &blks, int32_t mat, std::vector<int32_t> &trip);
+// sable_device.cu: column panel of the row-split SpMM kernels (V columns per
+// lane, L lanes per row)
+struct Panel { int V, L; };
+Panel spmm_panel(int cols, int64_t N, bool vec, bool vec2);
+// sable_device.cu: FP32 VBR blocks of SpMM in groups of rows (stores their rows of C)
+void vbr_group_pairs(const std::vector<Block> &blks, int32_t mat, std::vector<int32_t> &trip);
+sable_status launch_vbr_rows(const DevHybrid *mats, const int32_t *trip, int n_items, const float *B, int64_t ldb,
+                             float *C, int64_t ldc, const float *const *Bs, float *const *Cs, int N, int cols,
+                             int sm_count, cudaStream_t_ st);
 sable_status launch_vbr_tc(const DevHybrid *mats, const int32_t *trip, int n_trip, const float *B, int64_t ldb,
                            float *C, int64_t ldc, const float *const *Bs, float *const *Cs, int N, int sm_count,
                            int *err, cudaStream_t_ st, int terms);
 sable_status launch_spmv_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,
                                  const float *const *xs, float *const *ys, int sm_count, cudaStream_t_ st);
+sable_status launch_spmm_rows_grouped(const DevHybrid *mats, const int64_t *row_base, int count, int64_t rows,
+                                      const float *const *Bs, float *const *Cs, int N, bool vbrc, int cols, int depth,
+                                      int sm_count, cudaStream_t_ st);
 sable_status launch_spmm_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,
                                  const float *const *Bs, float *const *Cs, int N, bool vbrc, int sm_count,
                                  cudaStream_t_ st);

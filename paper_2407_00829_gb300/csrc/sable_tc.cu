@@ -36,6 +36,7 @@
 #include <cstring>
 
 #include "sable_internal.h"
+#include "sable_wait.cuh"
 
 namespace sable {
 
@@ -45,11 +46,17 @@ constexpr int kTcThreads = 128;
 constexpr int kTileM = 128, kTileN = 128, kTileK = 64;
 constexpr int kTileBytes = kTileM * kTileK * 2;        // 16 KB, A and B tiles alike
 constexpr unsigned kTmemCols = 128;
-constexpr long long kTcWait = 4000000000LL;            // ~2 s
+constexpr int kStageFloats = 4 * 32 * 33;               // epilogue transpose: 4 warps x 32 rows x 33
+
+template <int NS>
+union TileOrStage {
+  unsigned char a[NS][kTileBytes];   // A tile, one per bf16 term (K steps)
+  float stage[kStageFloats];         // epilogue: accumulator rows transposed for whole-row stores
+};
 
 template <int NS>
 struct TcShared {
-  alignas(1024) unsigned char a[NS][kTileBytes];   // A tile, one per bf16 term
+  alignas(1024) TileOrStage<NS> u;                 // the A tiles are free in the epilogue
   alignas(1024) unsigned char b[NS][kTileBytes];   // B tile, one per bf16 term
   uint64_t bar_a;     // A tiles landed
   uint64_t bar_mma;   // MMAs of the K step finished
@@ -57,28 +64,7 @@ struct TcShared {
   int dead;
 };
 
-__device__ __forceinline__ unsigned su32(const void *p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ bool bar_try(uint64_t *bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(su32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool bar_wait(uint64_t *bar, unsigned parity) {
-  if (bar_try(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!bar_try(bar, parity))
-    if (clock64() - t0 > kTcWait) return false;
-  return true;
-}
+__device__ __forceinline__ unsigned su32(const void *p) { return smem_u32(p); }
 
 // Shared-memory matrix descriptor: canonical K-major layout, no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(const void *p, unsigned lbo, unsigned sbo) {
@@ -95,7 +81,7 @@ template <int NS>
 __global__ void __launch_bounds__(kTcThreads, 1)
 vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ trip, int n_jobs, int ntn,
               const float *B0, int64_t ldb0, float *C0, int64_t ldc0, const float *const *Bs, float *const *Cs,
-              int N, int *err) {
+              int N, int *err, long long limit) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   // align the working area to 1024 bytes
   TcShared<NS> &S =
@@ -143,7 +129,7 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
         for (int sp = 0; sp < NS; ++sp)
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                  su32(S.a[sp])),
+                  su32(S.u.a[sp])),
               "l"(atiles[sp] + (size_t)kt * (kTileM * kTileK)), "r"((unsigned)kTileBytes), "r"(su32(&S.bar_a))
               : "memory");
       }
@@ -179,7 +165,10 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
-        if (!bar_wait(&S.bar_a, ph_a)) {
+        if (!mbar_wait(&S.bar_a, ph_a, limit)) {
+          // the A copies are still in flight: wait for them (bounded, longer)
+          // before this CTA can leave, then give up
+          (void)mbar_wait(&S.bar_a, ph_a, drain_limit(limit));
           atomicExch(err, (int)SABLE_ERR_TIMEOUT);
           S.dead = 1;
         } else {
@@ -192,7 +181,7 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
 #pragma unroll
             for (int pr = 0; pr < kPairs; ++pr) {
               const int ta = NS == 1 ? 0 : kPa[pr], tb = NS == 1 ? 0 : kPb[pr];
-              const uint64_t ad = smem_desc(S.a[ta] + ks * 256, 128, 1024);
+              const uint64_t ad = smem_desc(S.u.a[ta] + ks * 256, 128, 1024);
               const uint64_t bd = smem_desc(S.b[tb] + ks * 256, 128, 1024);
               const uint32_t acc = (kt > 0 || ks > 0 || pr > 0) ? 1u : 0u;
               asm volatile(
@@ -214,12 +203,13 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
         break;
       }
       // the tiles are overwritten next step: wait for the MMAs to finish reading them
-      const bool done = __all_sync(0xffffffffu, bar_wait(&S.bar_mma, ph_m));
-      ph_m ^= 1u;
-      if (!done) {
+      bool done = __all_sync(0xffffffffu, mbar_wait(&S.bar_mma, ph_m, limit));
+      if (!done) {   // the MMAs still read shared memory and write TMEM: wait (bounded, longer)
+        (void)__all_sync(0xffffffffu, mbar_wait(&S.bar_mma, ph_m, drain_limit(limit)));
         if (lane == 0) atomicExch(err, (int)SABLE_ERR_TIMEOUT);
         S.dead = 1;
       }
+      ph_m ^= 1u;
       __syncthreads();
       if (S.dead) ok = false;
     }
@@ -227,7 +217,7 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
     // epilogue: TMEM -> registers -> scale -> shared (transpose) -> C, whole
     // rows per store instruction.  The A/B tiles are free: the MMAs are done.
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float *stage = reinterpret_cast<float *>(&S.a[0][0]) + warp * (32 * 33);   // 32 rows x 33 (padded)
+    float *stage = S.u.stage + warp * (32 * 33);                             // 32 rows x 33 (padded)
     const int rbase = t * kTileM + 32 * warp;                             // first row of my warp in the block
 #pragma unroll 1
     for (int ch = 0; ch < kTileN / 32; ++ch) {
@@ -254,7 +244,10 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
       }
       __syncwarp();
     }
-    // all warps have read the accumulator before the next job overwrites it
+    // all warps have read the accumulator before the next job overwrites it;
+    // the staging writes (generic proxy) are ordered before the next job's
+    // bulk copies (async proxy) into the same bytes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -269,6 +262,8 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
 
 template <int NS>
 size_t tc_smem_bytes() { return sizeof(TcShared<NS>) + 1024; }
+static_assert(sizeof(TileOrStage<1>) >= (size_t)kStageFloats * 4 && sizeof(TileOrStage<3>) >= (size_t)kStageFloats * 4,
+              "epilogue staging area inside the A-tile region");
 
 // Host: bf16 of a float, round to nearest even (NaN kept quiet).
 static uint16_t to_bf16(float f) {
@@ -366,7 +361,8 @@ sable_status launch_vbr_tc(const DevHybrid *mats, const int32_t *trip, int n_tri
   auto k = terms == 1 ? vbr_tc_kernel<1> : vbr_tc_kernel<3>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
   const int grid = std::max(1, std::min((int)nj, per_sm * std::max(sm_count, 1)));
-  k<<<grid, kTcThreads, smem_req, st>>>(mats, trip, (int)nj, ntn, B, ldb, C, ldc, Bs, Cs, N, err);
+  k<<<grid, kTcThreads, smem_req, st>>>(mats, trip, (int)nj, ntn, B, ldb, C, ldc, Bs, Cs, N, err,
+                                        wait_limit_cycles());
   if (cudaGetLastError() != cudaSuccess) {
     (void)cudaGetLastError();
     return SABLE_ERR_CUDA;

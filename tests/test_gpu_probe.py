@@ -33,3 +33,40 @@ def test_row_probe_rejects(shape):
     out = torch.zeros(1, device="cuda")
     with pytest.raises(sable.SableError):
         sable.probe_row_gather(B, 1000, out)
+
+
+def test_bulk_copy_gather_probe_runs():
+    x = torch.rand(1_000_003, device="cuda")
+    out = torch.zeros(1, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    for count in (0, 1, 255, 257, 1 << 20):
+        sable.probe_bulk_gather(x, count, out, status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable():
+    """A wait that nothing satisfies ends with SABLE_ERR_TIMEOUT at the set
+    budget (no copy or tensor-core work in flight); afterwards the device
+    still runs the library's kernels."""
+    import numpy as np
+    import oracle
+    import synth
+    old = sable.wait_limit()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    try:
+        sable.set_wait_limit(2_000_000)              # ~1 ms
+        sable.probe_wait_limit(status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 6               # SABLE_ERR_TIMEOUT
+    finally:
+        sable.set_wait_limit(old)
+    assert sable.wait_limit() == old
+    A = synth.mixed_matrix(np.random.default_rng(3), 2000, 10.0)
+    P = sable.plan_from(A, [(sable.VDIA, None), (sable.CSR, None)])
+    x = synth.dense_operand(1, A["n"])
+    y = torch.empty(A["m"], device="cuda")
+    P.spmv(torch.from_numpy(x).cuda(), y)
+    torch.cuda.synchronize()
+    assert oracle.normwise_err(y.cpu().numpy(), oracle.spmv(A["m"], A["row"], A["col"], A["val"], x)) <= 1e-5
+    P.close()

@@ -214,3 +214,13 @@ def test_library_recovers_separated_planted_blocks(seed):
                             upload=False)
         assert P.blocks().tolist() == [[20, 4, 15, 60]]
         P.close()
+
+
+def test_wait_limit_bounds_checked_on_the_host():
+    L = sable.lib()
+    old = sable.wait_limit()
+    assert L.sable_set_wait_limit(10) == 1 and L.sable_set_wait_limit(1 << 41) == 1   # SABLE_ERR_INVALID
+    assert sable.wait_limit() == old
+    sable.set_wait_limit(123456)
+    assert sable.wait_limit() == 123456
+    sable.set_wait_limit(old)

@@ -295,15 +295,14 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
     # every variant at the default tiling, then the hybrid variants each at the
     # tiling the autotuner picks for it; plain CSR keeps the best it got
     default = run_variants(("fp32", "fp32_split", "bf16_blocks", "plain_csr"))
-    out["autotune"] = {"default": {"spmm_rows": 32, "spmm_elems": 4096},
+    out["autotune"] = {"default": {"spmm_cols": 0, "spmm_depth": 4},
                        "default_tiling_ms": {k_: v["ms"] for k_, v in default.items()}}
     plain_best = default["plain_csr"]
     for name, op in (("fp32", sable.TUNE_SPMM_FP32), ("fp32_split", sable.TUNE_SPMM_FP32_SPLIT),
                      ("bf16_blocks", sable.TUNE_SPMM_BF16)):
         t0 = time.perf_counter()
         tuned, _ = P.autotune(op, B, C, reps=5, use_cache=False, stream=stream)
-        out["autotune"][name] = {"spmm_rows": tuned["spmm_rows"], "spmm_elems": tuned["spmm_elems"],
-                                 "spmm_cols": tuned["spmm_cols"], "spmm_depth": tuned["spmm_depth"],
+        out["autotune"][name] = {"spmm_cols": tuned["spmm_cols"], "spmm_depth": tuned["spmm_depth"],
                                  "tune_s": round(time.perf_counter() - t0, 2)}
         got = run_variants((name, "plain_csr"))
         res[name] = got[name]
@@ -314,8 +313,9 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
         order = np.lexsort((A["col"], A["row"]))
         crow = np.zeros(A["m"] + 1, dtype=np.int64)
         np.add.at(crow, A["row"].astype(np.int64) + 1, 1)
-        Acs = torch.sparse_csr_tensor(torch.from_numpy(np.cumsum(crow)).to(dev),
-                                      torch.from_numpy(A["col"][order].astype(np.int64)).to(dev),
+        # int32 row pointers and columns (8 bytes per entry, as the library's CSR)
+        Acs = torch.sparse_csr_tensor(torch.from_numpy(np.cumsum(crow).astype(np.int32)).to(dev),
+                                      torch.from_numpy(A["col"][order].astype(np.int32)).to(dev),
                                       torch.from_numpy(A["val"][order]).to(dev), size=(A["m"], A["n"]))
         for _ in range(3):
             torch.sparse.mm(Acs, B)
@@ -452,8 +452,8 @@ def run_batch(args):
         tm, tm_ms = tune.tune_batch(plans, "spmm_bf16", Bs, Cs, N=N, stream=stream)
         autotune = {"spmv": {"chosen": [tv["spmv_rows"], tv["spmv_bytes"]], "ms_chosen": min(tv_ms.values()),
                              "ms_default": tv_ms[(512, 48 << 10)]},
-                    "spmm_bf16": {"chosen": [tm["spmm_rows"], tm["spmm_elems"]], "ms_chosen": min(tm_ms.values()),
-                                  "ms_default": tm_ms[(32, 4096)]},
+                    "spmm_bf16": {"chosen": {"spmm_cols": tm["spmm_cols"], "spmm_depth": tm["spmm_depth"]},
+                                  "ms_chosen": min(tm_ms.values()), "ms_default": tm_ms[(0, 4)]},
                     "tune_s": round(time.perf_counter() - t0, 1)}
     B = sable.Batch(plans)
     nnz = sum(i["nnz"] for i in infos)
@@ -688,9 +688,9 @@ def main():
         rows, cols, vals = A["row"][order], A["col"][order], A["val"][order]
         crow = np.zeros(A["m"] + 1, dtype=np.int64)
         np.add.at(crow, rows.astype(np.int64) + 1, 1)
-        crow = np.cumsum(crow)
+        crow = np.cumsum(crow).astype(np.int32)   # int32 indices: 8 bytes per entry, as the library's CSR
         for i in range(reps):
-            cs.append(torch.sparse_csr_tensor(torch.from_numpy(crow).to(dev), torch.from_numpy(cols.astype(np.int64)).to(dev),
+            cs.append(torch.sparse_csr_tensor(torch.from_numpy(crow).to(dev), torch.from_numpy(cols.astype(np.int32)).to(dev),
                                               torch.from_numpy(vals).to(dev), size=(A["m"], A["n"])))
         for i in range(5):
             torch.mv(cs[i % reps], xs[i % reps])

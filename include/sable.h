@@ -215,40 +215,36 @@ sable_status sable_plan_update_values(sable_plan_t plan, const float *val, void 
  * sorting the COO input again.  Errors: SABLE_ERR_INVALID; SABLE_ERR_CUDA. */
 sable_status sable_plan_reset(sable_plan_t plan);
 
-/* Tuning of the row tiles one launch works on; takes effect at the next
+/* Tuning of the row tiles of the SpMV launch; takes effect at the next
  * upload.  spmv_rows: rows of an SpMV tile, a multiple of 4 in [4, 1024];
- * spmv_bytes: target algorithmic bytes per SpMV tile; spmm_rows: rows of an
- * SpMM tile, a multiple of 4 in [4, 256]; spmm_elems: target stored cells +
- * entries per SpMM tile.  The SpMM tiles serve the grouped launches of
- * sable_batch_spmm; one matrix's SpMM is row split (a warp per row) and
- * depends only on the column panel and depth below.  Errors:
- * SABLE_ERR_INVALID. */
-sable_status sable_plan_set_tiling(sable_plan_t plan, int32_t spmv_rows, int64_t spmv_bytes,
-                                   int32_t spmm_rows, int64_t spmm_elems);
+ * spmv_bytes: target algorithmic bytes per SpMV tile (>= 64).  SpMM is row
+ * split (a lane group per row) and depends only on the column panel and depth
+ * below.  Errors: SABLE_ERR_INVALID. */
+sable_status sable_plan_set_tiling(sable_plan_t plan, int32_t spmv_rows, int64_t spmv_bytes);
 
-/* The plan's current tiling (the four values of sable_plan_set_tiling). */
+/* The plan's current tiling. */
 typedef struct {
   int32_t spmv_rows;
   int64_t spmv_bytes;
-  int32_t spmm_rows;
-  int64_t spmm_elems;
   int32_t spmm_cols;   /* 0 = widest panel the operands allow; else 32, 64 or 128 */
-  int32_t spmm_depth;  /* B rows in flight per warp in SpMM: 4 or 8 */
+  int32_t spmm_depth;  /* B rows in flight per lane group in SpMM: 4 or 8 */
 } sable_tiling;
 sable_status sable_plan_get_tiling(sable_plan_t plan, sable_tiling *out);
 
-/* Columns of C (and B) one SpMM CTA works on: 128 (four per lane; needs N,
- * ldb, ldc multiples of 4 and 16-byte aligned B, C), 64 (two per lane; even
- * N, ldb, ldc and 8-byte alignment) or 32; 0 picks the widest the operands
- * allow.  The column panels of one launch run one after another, so a
- * narrower panel keeps a smaller slice of B live in L2 while its rows are
- * gathered.  A panel the operands do not allow falls back to 32.  Takes
- * effect at the next SpMM call.  Errors: SABLE_ERR_INVALID. */
+/* Columns of C (and B) one SpMM CTA works on: 128, 64 or 32.  With N, ldb,
+ * ldc multiples of 4 and 16-byte aligned B, C every lane holds four columns
+ * and a group of 32, 16 or 8 lanes owns a row, so narrow panels put several
+ * rows on a warp; otherwise 64 means two columns per lane (even N, ldb, ldc,
+ * 8-byte alignment) and 32 one.  0 picks the widest the operands allow, or
+ * for N <= 32 (<= 64) the 32- (64-) column panel.  The column panels of one
+ * launch run one after another, so a narrower panel keeps a smaller slice of
+ * B live in L2 while its rows are gathered.  Takes effect at the next SpMM
+ * call.  Errors: SABLE_ERR_INVALID. */
 sable_status sable_plan_set_spmm_cols(sable_plan_t plan, int32_t cols);
 
-/* B rows each warp has in flight in SpMM: 4 (default) or 8 (more loads in
- * flight, more registers: at most 4 CTAs per SM; used with 64- and 128-column
- * panels).  Takes effect at the next SpMM call.  Errors: SABLE_ERR_INVALID. */
+/* B rows each lane group has in flight in SpMM: 4 (default) or 8 (more loads
+ * in flight, more registers: at most 4 CTAs per SM).  Takes effect at the
+ * next SpMM call.  Errors: SABLE_ERR_INVALID. */
 sable_status sable_plan_set_spmm_depth(sable_plan_t plan, int32_t depth);
 
 /* Autotuner (no counterpart in the paper, which runs one generated kernel per
@@ -260,8 +256,8 @@ sable_status sable_plan_set_spmm_depth(sable_plan_t plan, int32_t depth);
  * the timed launches read and overwrite.  Candidates: SpMV rows {128, 256,
  * 512, 1024} x bytes {16K, 48K, 160K}, and 1024 rows with the bytes that cut
  * the plan into 1, 2 or 3 full waves of the CTAs the GPU holds at once; SpMM
- * (column panel, rows in flight) in {(128, 4), (128, 8), (64, 4), (64, 8),
- * (32, 4)}; the other op's tiling is kept.  Each candidate is
+ * (column panel, rows in flight) in {128, 64, 32} x {4, 8}; the other op's
+ * tiling is kept.  Each candidate is
  * uploaded (sable_plan_upload, which reallocates the plan's device tables and
  * waits for the device), run twice, then timed as the best of two rounds of
  * `reps` back-to-back launches.  The winner is remembered per shape class
@@ -456,6 +452,16 @@ sable_status sable_error_norms(const float *y, const double *ref, int64_t count,
  * debug build's checks recorded one).
  * Errors: SABLE_ERR_ORDER before upload; SABLE_ERR_CUDA. */
 sable_status sable_plan_device_error(sable_plan_t plan, int32_t *out);
+
+/* Testing hook, no counterpart in the paper: allocation-failure injection.
+ * after >= 0 lets that many of the library's guarded allocations (plan
+ * creation, extraction, the upload's host staging and its device
+ * allocation, a batch's device allocation) pass and makes the next one fail
+ * as if memory ran out, once; after < 0 turns injection off.  The failing
+ * call returns SABLE_ERR_OOM, frees what it had allocated and leaves other
+ * plans untouched (a plan that failed keeps SABLE_ERR_OOM as its sticky
+ * status).  Process-wide; not for production use. */
+void sable_debug_fail_allocations(int64_t after);
 
 /* First error recorded on the plan (SABLE_OK if none). */
 sable_status sable_plan_status(sable_plan_t plan);

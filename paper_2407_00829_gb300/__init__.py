@@ -38,7 +38,7 @@ EXPORTED = [
     "sable_error_workspace_bytes", "sable_error_norms", "sable_plan_get_tiling", "sable_autotune",
     "sable_autotune_cache_clear", "sable_plan_set_spmm_cols", "sable_plan_update_values",
     "sable_plan_set_spmm_depth", "sable_plan_device_error", "sable_probe_bulk_gather", "sable_set_wait_limit",
-    "sable_get_wait_limit", "sable_probe_wait_limit",
+    "sable_get_wait_limit", "sable_probe_wait_limit", "sable_debug_fail_allocations",
 ]
 
 NFEAT = 24
@@ -96,7 +96,7 @@ def lib():
             "sable_plan_get_vdia_values": ([p, p], i32),
             "sable_plan_get_vbr_values": ([p, p], i32),
             "sable_plan_get_csr": ([p, p, p, p], i32),
-            "sable_plan_set_tiling": ([p, i32, i64, i32, i64], i32),
+            "sable_plan_set_tiling": ([p, i32, i64], i32),
             "sable_plan_status": ([p], i32),
             "sable_plan_destroy": ([p], i32),
             "sable_status_string": ([i32], ctypes.c_char_p),
@@ -123,6 +123,7 @@ def lib():
             "sable_set_wait_limit": ([i64], i32),
             "sable_get_wait_limit": ([], i64),
             "sable_probe_wait_limit": ([p, p], i32),
+            "sable_debug_fail_allocations": ([i64], None),
             "sable_plan_set_spmm_cols": ([p, i32], i32),
             "sable_plan_update_values": ([p, p, p], i32),
             "sable_plan_set_spmm_depth": ([p, i32], i32),
@@ -169,8 +170,8 @@ def _dptr(t) -> int:
 
 
 class Tiling(ctypes.Structure):
-    _fields_ = [("spmv_rows", ctypes.c_int32), ("spmv_bytes", ctypes.c_int64), ("spmm_rows", ctypes.c_int32),
-                ("spmm_elems", ctypes.c_int64), ("spmm_cols", ctypes.c_int32), ("spmm_depth", ctypes.c_int32)]
+    _fields_ = [("spmv_rows", ctypes.c_int32), ("spmv_bytes", ctypes.c_int64), ("spmm_cols", ctypes.c_int32),
+                ("spmm_depth", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -286,10 +287,8 @@ class Plan:
         _check(lib().sable_extract(self._h), "sable_extract")
         return self
 
-    def set_tiling(self, spmv_rows=512, spmv_bytes=48 * 1024, spmm_rows=32, spmm_elems=4096, spmm_cols=None,
-                   spmm_depth=None):
-        _check(lib().sable_plan_set_tiling(self._h, spmv_rows, spmv_bytes, spmm_rows, spmm_elems),
-               "set_tiling")
+    def set_tiling(self, spmv_rows=512, spmv_bytes=48 * 1024, spmm_cols=None, spmm_depth=None):
+        _check(lib().sable_plan_set_tiling(self._h, spmv_rows, spmv_bytes), "set_tiling")
         if spmm_cols is not None:
             _check(lib().sable_plan_set_spmm_cols(self._h, spmm_cols), "set_spmm_cols")
         if spmm_depth is not None:

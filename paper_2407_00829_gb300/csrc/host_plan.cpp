@@ -3,6 +3,7 @@
 // "Initialize" / "Extract"), the completeness check (Section 3, "Dispatch"),
 // and host exports.  No CUDA call is made here.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -13,6 +14,22 @@
 #include "sable_internal.h"
 
 using namespace sable;
+
+namespace sable {
+namespace {
+std::atomic<int64_t> g_fail_after{-1};   // guarded allocations to let pass; -1 = injection off
+}
+bool alloc_fails() {
+  int64_t v = g_fail_after.load(std::memory_order_relaxed);
+  while (v >= 0) {
+    if (g_fail_after.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return v == 0;
+  }
+  return false;
+}
+void alloc_point() {
+  if (alloc_fails()) throw std::bad_alloc();
+}
+}  // namespace sable
 
 namespace sable {
 
@@ -90,6 +107,7 @@ sable_status sable_plan_create(int64_t m, int64_t n, int64_t nnz, const int32_t 
   sable_plan_s *P = new (std::nothrow) sable_plan_s();
   if (!P) return SABLE_ERR_OOM;
   try {
+    alloc_point();
     P->m = m;
     P->n = n;
     // bucket by row, keeping input order, then order each row by column
@@ -189,6 +207,7 @@ sable_status sable_extract(sable_plan_t P) {
   if (P->sticky) return P->sticky;
   if (P->extracted) return SABLE_ERR_ORDER;
   try {
+    alloc_point();
     const Csr &C = P->canon;
     const int64_t nnz = C.nnz();
     std::vector<int32_t> region(nnz, -1);
@@ -419,16 +438,11 @@ sable_status sable_plan_get_csr(sable_plan_t P, int64_t *row_ptr, int32_t *col, 
   return SABLE_OK;
 }
 
-sable_status sable_plan_set_tiling(sable_plan_t P, int32_t spmv_rows, int64_t spmv_bytes,
-                                   int32_t spmm_rows, int64_t spmm_elems) {
+sable_status sable_plan_set_tiling(sable_plan_t P, int32_t spmv_rows, int64_t spmv_bytes) {
   if (!P) return SABLE_ERR_INVALID;
-  if (spmv_rows < 4 || spmv_rows > kRangeRows || spmv_rows % 4 || spmv_bytes < 64 || spmm_rows < 4 ||
-      spmm_rows > 256 || spmm_rows % 4 || spmm_elems < 1)
-    return SABLE_ERR_INVALID;
+  if (spmv_rows < 4 || spmv_rows > kRangeRows || spmv_rows % 4 || spmv_bytes < 64) return SABLE_ERR_INVALID;
   P->tiling.rows_per_item = spmv_rows;
   P->tiling.item_bytes = spmv_bytes;
-  P->tiling.rows_per_item_mm = spmm_rows;
-  P->tiling.item_elems_mm = spmm_elems;
   return SABLE_OK;
 }
 
@@ -445,5 +459,9 @@ sable_status sable_plan_set_spmm_depth(sable_plan_t P, int32_t depth) {
 }
 
 sable_status sable_plan_status(sable_plan_t P) { return P ? P->sticky : SABLE_ERR_INVALID; }
+
+void sable_debug_fail_allocations(int64_t after) {
+  sable::g_fail_after.store(after < 0 ? -1 : after, std::memory_order_relaxed);
+}
 
 }  // extern "C"

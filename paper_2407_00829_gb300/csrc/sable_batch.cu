@@ -23,14 +23,14 @@ struct sable_batch_s {
   int device = -1, sm_count = 1;
   char *blob = nullptr;
   const DevHybrid *mats = nullptr;
-  const DevItem *items_v = nullptr, *items_m = nullptr;
+  const DevItem *items_v = nullptr;
   const int32_t *trip = nullptr;
   const int32_t *fg = nullptr;         // (matrix, block, row group) triples of the FP32 block kernel
   int n_fg = 0;
   const int64_t *row_base = nullptr;   // rows of the matrices before each one (count + 1)
   int64_t rows = 0;                    // all rows of the batch
   int *err = nullptr;
-  int n_v = 0, n_m = 0, n_trip = 0, rows_v = 0, rows_m = 0;
+  int n_v = 0, n_trip = 0, rows_v = 0;
 };
 
 struct sable_graph_s {
@@ -109,7 +109,7 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
   sable_batch_s *b = new (std::nothrow) sable_batch_s();
   if (!b) return SABLE_ERR_OOM;
   std::vector<DevHybrid> mats;
-  std::vector<DevItem> iv, im;
+  std::vector<DevItem> iv;
   std::vector<int32_t> trip, fg;
   std::vector<int64_t> row_base(1, 0);
   try {
@@ -125,10 +125,6 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
         it.mat = i;
         iv.push_back(it);
       }
-      for (DevItem it : P->h_items_m) {
-        it.mat = i;
-        im.push_back(it);
-      }
       for (size_t k = 0; k + 2 < P->h_trip.size(); k += 3) {
         trip.push_back(i);
         trip.push_back(P->h_trip[k + 1]);
@@ -141,7 +137,6 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
       }
       row_base.push_back(row_base.back() + P->m);
       b->rows_v = std::max(b->rows_v, P->dev.spmv.rows_max);
-      b->rows_m = std::max(b->rows_m, P->dev.spmm.rows_max);
     }
   } catch (const std::bad_alloc &) {
     delete b;
@@ -149,10 +144,10 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
   }
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t s_err = 256, s_m = al(mats.size() * sizeof(DevHybrid)), s_v = al(iv.size() * sizeof(DevItem)),
-               s_i = al(im.size() * sizeof(DevItem)), s_t = al(trip.size() * sizeof(int32_t)),
+               s_t = al(trip.size() * sizeof(int32_t)),
                s_r = al(row_base.size() * sizeof(int64_t)), s_f = al(fg.size() * sizeof(int32_t));
-  const size_t total = s_err + s_m + s_v + s_i + s_t + s_r + s_f;
-  if (cudaMalloc(&b->blob, total) != cudaSuccess) {
+  const size_t total = s_err + s_m + s_v + s_t + s_r + s_f;
+  if (alloc_fails() || cudaMalloc(&b->blob, total) != cudaSuccess) {
     (void)cudaGetLastError();
     delete b;
     return SABLE_ERR_OOM;
@@ -164,8 +159,6 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
   p += s_m;
   b->items_v = reinterpret_cast<const DevItem *>(p);
   p += s_v;
-  b->items_m = reinterpret_cast<const DevItem *>(p);
-  p += s_i;
   b->trip = reinterpret_cast<const int32_t *>(p);
   p += s_t;
   b->row_base = reinterpret_cast<const int64_t *>(p);
@@ -176,8 +169,6 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
     e = cudaMemcpy((void *)b->mats, mats.data(), mats.size() * sizeof(DevHybrid), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !iv.empty())
     e = cudaMemcpy((void *)b->items_v, iv.data(), iv.size() * sizeof(DevItem), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !im.empty())
-    e = cudaMemcpy((void *)b->items_m, im.data(), im.size() * sizeof(DevItem), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !trip.empty())
     e = cudaMemcpy((void *)b->trip, trip.data(), trip.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
@@ -191,7 +182,6 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
     return SABLE_ERR_CUDA;
   }
   b->n_v = (int)iv.size();
-  b->n_m = (int)im.size();
   b->n_trip = (int)(trip.size() / 3);
   b->n_fg = (int)(fg.size() / 3);
   b->rows = row_base.back();
@@ -208,7 +198,7 @@ sable_status sable_batch_spmv(sable_batch_t b, const float *const *x, float *con
 
 sable_status sable_batch_spmm(sable_batch_t b, const float *const *B, int64_t N, float *const *C,
                               sable_precision prec, void *stream) {
-  if (!b || (b->n_m > 0 && (!B || !C))) return SABLE_ERR_INVALID;
+  if (!b || (b->rows > 0 && (!B || !C))) return SABLE_ERR_INVALID;
   return batch_spmm_launch(b, B, N, C, prec, (cudaStream_t)stream);
 }
 
@@ -219,7 +209,7 @@ sable_status sable_batch_graph_spmv(sable_batch_t b, const float *const *x, floa
 
 sable_status sable_batch_graph_spmm(sable_batch_t b, const float *const *B, int64_t N, float *const *C,
                                     sable_precision prec, sable_graph_t *out) {
-  if (!b || !out || (b->n_m > 0 && (!B || !C))) return SABLE_ERR_INVALID;
+  if (!b || !out || (b->rows > 0 && (!B || !C))) return SABLE_ERR_INVALID;
   return capture(b, out, true, B, N, C, prec);
 }
 

@@ -1,17 +1,16 @@
-// Device side of libsable: table upload, the fused hybrid SpMM kernel (FP32)
-// and the C-ABI compute entry points.  (The SpMV kernel is in sable_spmv.cu.)
-// One launch computes every format for a row tile ("item") and writes each
-// output row once, instead of the paper's sequence of dispatches that each
-// accumulate into a shared output (Section 3.4).
+// Device side of libsable: table upload, the row-split SpMM kernels (FP32
+// arithmetic) and the C-ABI compute entry points.  (The SpMV kernel is in
+// sable_spmv.cu, the tensor-core block kernel in sable_tc.cu.)
 //
-// SpMM, per item (rows [r0, r1)) and column tile of B/C:
-//   A. VDIA: every segment touching the rows (Section 4.2.1 layout); a warp
-//      owns a row, lanes own columns, each band value is reused over the
-//      tile's columns.
-//   B. VBR: every block touching the rows; column-major blocks (Appendix B).
-//   C. CSR remainder: the tile's entries split evenly over warps; lanes own
-//      columns; partial rows are merged with shared atomics.
-//   The accumulators live in shared memory and are stored once per row.
+// SpMM C = A B is row split: a group of lanes owns one row of C (a panel of
+// its columns) and sums, in registers, one stream of entries: the row's VDIA
+// diagonals (Section 4.2.1 layout), its FP32 VBR block columns (column-major,
+// Appendix B) and its CSR remainder entries, one B row per entry, then stores
+// the row once, instead of the paper's sequence of dispatches that each
+// accumulate into a shared output (Section 3.4).  VBR blocks whose rows no
+// other block shares are instead multiplied first, either on the tensor cores
+// (sable_tc.cu) or FP32 in groups of 8 block rows that share each B row
+// read, and their rows of C stored; the row-split launch adds the rest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -70,163 +69,6 @@ template <> struct VecT<1> {
   __device__ static void add_to(float *p, const T &a) { p[0] += a; }
   __device__ static void atomic_add_to(float *p, const T &a) { atomicAdd(p, a); }
 };
-
-// Tiled SpMM, the form of the grouped many-matrix launch (one matrix's SpMM
-// is row split, below): C[r0:r1, n0:n0+NT] of one row tile, its parts summed
-// into a shared tile and stored once.  V = 4 needs N, ldb, ldc multiples of 4
-// and 16-byte aligned B, C.  Shared tile: rows_max x NT floats, then row
-// pointers.
-template <int THREADS, int V, bool VBRC, int U = 4>
-__device__ __forceinline__ void spmm_tile(const DevHybrid &A, const DevItem &I, const float *__restrict__ B,
-                                          int64_t ldb, float *__restrict__ C, int64_t ldc, int N, float *cs,
-                                          int *rps) {
-  using Vt = VecT<V>;
-  using T = typename Vt::T;
-  constexpr int NT = 32 * V;
-  constexpr int NW = THREADS / 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n0 = blockIdx.y * NT;
-  const int lc = V * lane;                       // this lane's first column in the tile
-  const bool lane_ok = n0 + lc < N;
-  const unsigned n = (unsigned)A.n;
-  {
-    const int r0 = I.r0, R = I.r1 - I.r0;
-    for (int i = tid; i < R * NT; i += THREADS) cs[i] = 0.f;
-    for (int i = tid; i <= R; i += THREADS) rps[i] = __ldg(A.rp + r0 + i);
-    __syncthreads();
-
-    // ---- A. VDIA.  Item rows go to warps in groups of four: rows 4g .. 4g+3
-    // belong to warp g % NW in phases A and B, so their shared-memory sums
-    // need no atomics.
-    for (int q = I.seg_lo; q < I.seg_hi; ++q) {
-      const DevSeg s = A.segs[__ldg(A.spmm.iseg + q)];
-      const int ia = max(r0, s.row0) - r0, ib = min(I.r1, s.row0 + s.nrows) - r0;
-      for (int g = (ia >> 2) + ((warp - (ia >> 2) % NW) + NW) % NW; 4 * g < ib; g += NW) {
-        for (int i = max(4 * g, ia); i < min(4 * g + 4, ib); ++i) {
-          const int r = r0 + i;
-          T acc = Vt::zero();
-          const float *vp = A.vdia + s.val_off + (r - s.base);
-          for (int k = 0; k < s.ndiag; ++k) {
-            const int c = r + s.off_lo + k;
-            if ((unsigned)c >= n) continue;
-            const float v = __ldcs(vp + (int64_t)k * s.ld);
-            if (lane_ok) Vt::fma(acc, v, Vt::load(B + (int64_t)c * ldb + n0 + lc));
-          }
-          if (lane_ok) Vt::add_to(cs + i * NT + lc, acc);
-        }
-      }
-    }
-    // ---- B. VBR: already multiplied on the tensor cores into C (VBRC), or FP32
-    // FMA with four block rows per warp, so that each B row loaded serves four
-    // rows of the block
-    if (VBRC && A.n_tc > 0) {   // a matrix whose blocks share rows keeps them on FMA
-      for (int q = I.blk_lo; q < I.blk_hi; ++q) {
-        const DevBlk b = A.spmm.pblk[q];
-        const int ia = max(r0, b.r0) - r0, ib = min(I.r1, b.r0 + b.nr) - r0;
-        for (int g = (ia >> 2) + ((warp - (ia >> 2) % NW) + NW) % NW; 4 * g < ib; g += NW)
-          for (int i = max(4 * g, ia); i < min(4 * g + 4, ib); ++i)
-            if (lane_ok) Vt::add_to(cs + i * NT + lc, Vt::load_once(C + (int64_t)(r0 + i) * ldc + n0 + lc));
-      }
-    } else
-    for (int q = I.blk_lo; q < I.blk_hi; ++q) {
-      const DevBlk b = A.blks[__ldg(A.spmm.iblk + q)];
-      const int ia = max(r0, b.r0) - r0, ib = min(I.r1, b.r0 + b.nr) - r0;
-      for (int g = (ia >> 2) + ((warp - (ia >> 2) % NW) + NW) % NW; 4 * g < ib; g += NW) {
-        const int i0 = max(4 * g, ia), nrow = min(4 * g + 4, ib) - i0;   // 1..4 rows of this block
-        const float *ap = A.vbr + b.val_off + (r0 + i0 - b.r0);
-        const float *bp = B + (int64_t)b.c0 * ldb + n0 + lc;
-        T a0 = Vt::zero(), a1 = Vt::zero(), a2 = Vt::zero(), a3 = Vt::zero();
-        for (int c = 0; c < b.nc; ++c) {
-          const float *col = ap + (int64_t)c * b.nr;
-          const float w0 = __ldg(col);
-          const float w1 = nrow > 1 ? __ldg(col + 1) : 0.f;
-          const float w2 = nrow > 2 ? __ldg(col + 2) : 0.f;
-          const float w3 = nrow > 3 ? __ldg(col + 3) : 0.f;
-          if (lane_ok) {
-            const T bv = Vt::load(bp + (int64_t)c * ldb);
-            Vt::fma(a0, w0, bv);
-            Vt::fma(a1, w1, bv);
-            Vt::fma(a2, w2, bv);
-            Vt::fma(a3, w3, bv);
-          }
-        }
-        if (lane_ok) {
-          Vt::add_to(cs + i0 * NT + lc, a0);
-          if (nrow > 1) Vt::add_to(cs + (i0 + 1) * NT + lc, a1);
-          if (nrow > 2) Vt::add_to(cs + (i0 + 2) * NT + lc, a2);
-          if (nrow > 3) Vt::add_to(cs + (i0 + 3) * NT + lc, a3);
-        }
-      }
-    }
-    __syncthreads();
-
-    // ---- C. CSR remainder: the tile's entries split evenly over warps
-    const int pb = rps[0], pe = rps[R];
-    const int per = (pe - pb + NW - 1) / NW;
-    const int pa = pb + warp * per, pz = min(pe, pa + per);
-    if (pa < pz) {
-      int lo = 0, hi = R;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (rps[mid] <= pa) lo = mid;
-        else hi = mid;
-      }
-      int cur = lo, nxt = rps[lo + 1];
-      T acc = Vt::zero();
-      for (int base = pa; base < pz; base += 32) {
-        const int p = base + lane;
-        float v = 0.f;
-        int c = 0;
-        if (p < pz) {
-          v = __ldcs(A.cv + p);
-          c = __ldcs(A.ci + p);
-        }
-        const int cnt = min(32, pz - base);
-        for (int j = 0; j < cnt; j += U) {   // U entries' B rows in flight per warp
-          T bj[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int cu = __shfl_sync(kFull, c, (j + u) & 31);
-            bj[u] = (lane_ok && j + u < cnt) ? Vt::load(B + (int64_t)cu * ldb + n0 + lc) : Vt::zero();
-          }
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const float vu = __shfl_sync(kFull, v, (j + u) & 31);   // the entry's value, fetched when used
-            if (j + u < cnt) {
-              const int pp = base + j + u;
-              if (pp >= nxt) {
-                if (lane_ok) Vt::atomic_add_to(cs + (cur)*NT + lc, acc);
-                acc = Vt::zero();
-                while (pp >= nxt) {
-                  ++cur;
-                  nxt = rps[cur + 1];
-                }
-              }
-              Vt::fma(acc, vu, bj[u]);
-            }
-          }
-        }
-      }
-      if (lane_ok) Vt::atomic_add_to(cs + cur * NT + lc, acc);
-    }
-    __syncthreads();
-    // ---- store the tile
-    if (lane_ok) {
-      for (int i = warp; i < R; i += NW) {
-        const float *src = cs + i * NT + lc;
-        float *dst = C + (int64_t)(r0 + i) * ldc + n0 + lc;
-        if (V == 4) {
-          __stcs(reinterpret_cast<float4 *>(dst), *reinterpret_cast<const float4 *>(src));
-        } else if (V == 2) {
-          __stcs(reinterpret_cast<float2 *>(dst), *reinterpret_cast<const float2 *>(src));
-        } else {
-          __stcs(dst, src[0]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // Row-split SpMM works on lane groups: a group of L lanes (8, 16 or 32) owns
 // one row of C and V columns per lane, so a warp holds 32 / L rows at once
@@ -514,21 +356,6 @@ spmm_rows_grouped_kernel(const DevHybrid *__restrict__ mats, const int64_t *__re
   }
 }
 
-// Many matrices in one launch (B_i: n_i x N, C_i: m_i x N, both with leading
-// dimension N).
-template <int THREADS, int V, bool VBRC>
-__global__ void __launch_bounds__(THREADS)
-spmm_grouped_kernel(const DevHybrid *__restrict__ mats, const DevItem *__restrict__ items, int n_items,
-                    int rows_max, const float *const *__restrict__ Bs, float *const *__restrict__ Cs, int N) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float *cs = reinterpret_cast<float *>(smem_raw);
-  int *rps = reinterpret_cast<int *>(cs + rows_max * 32 * V);
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const DevItem I = items[it];
-    spmm_tile<THREADS, V, VBRC>(mats[I.mat], I, Bs[I.mat], N, Cs[I.mat], N, N, cs, rps);
-  }
-}
-
 // ------------------------------------------------------------------ host helpers
 struct HostItems {
   std::vector<DevItem> items;
@@ -538,11 +365,12 @@ struct HostItems {
   int32_t rows_max = 0;
 };
 
-// Cut rows into tiles of at most rows_max rows (multiples of 4) whose summed
-// per-row cost stays near `target`; list the segments/blocks touching each.
+// Cut rows into SpMV tiles of at most rows_max rows (multiples of 4) whose
+// summed per-row algorithmic bytes stay near `target`; list the
+// segments/blocks touching each.
 static HostItems build_items(int64_t m, const std::vector<Segment> &segs,
                              const std::vector<Block> &blks, const std::vector<int64_t> &rp,
-                             int rows_max, int64_t target, bool spmm) {
+                             int rows_max, int64_t target) {
   std::vector<int64_t> vd(m + 1, 0), vb(m + 1, 0);
   for (auto &s : segs) {
     vd[s.row0] += s.ndiag;
@@ -558,7 +386,7 @@ static HostItems build_items(int64_t m, const std::vector<Segment> &segs,
   }
   auto cost = [&](int64_t i) -> int64_t {
     const int64_t c = rp[i + 1] - rp[i];
-    return spmm ? 1 + vd[i] + vb[i] + c : 8 + 4 * vd[i] + 4 * vb[i] + 8 * c;
+    return 8 + 4 * vd[i] + 4 * vb[i] + 8 * c;
   };
   HostItems H;
   size_t sp = 0, bp = 0;
@@ -632,7 +460,7 @@ struct Staging {
   std::vector<float> vbr_scale;
   std::vector<float> cv, pcv;
   std::vector<int32_t> srp, sref;
-  HostItems it_v, it_m, pit_v, pit_m;
+  HostItems it_v, pit_v;
 };
 
 }  // namespace sable
@@ -658,6 +486,7 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   }
   Staging *S = nullptr;
   try {
+    alloc_point();
     S = new Staging();
     const Hybrid &H = P->hyb;
     const Csr &Cn = P->canon;
@@ -743,12 +572,10 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
     S->pci.resize(S->pci.size() + kCsrPad, 0);
     S->pcv.resize(S->pcv.size() + kCsrPad, 0.0f);
     const Tiling &T = P->tiling;
-    S->it_v = build_items(P->m, H.segs, H.blks, H.crp, T.rows_per_item, T.item_bytes, false);
-    S->it_m = build_items(P->m, H.segs, H.blks, H.crp, T.rows_per_item_mm, T.item_elems_mm, true);
+    S->it_v = build_items(P->m, H.segs, H.blks, H.crp, T.rows_per_item, T.item_bytes);
     const std::vector<Segment> no_s;
     const std::vector<Block> no_b;
-    S->pit_v = build_items(P->m, no_s, no_b, Cn.rp, T.rows_per_item, T.item_bytes, false);
-    S->pit_m = build_items(P->m, no_s, no_b, Cn.rp, T.rows_per_item_mm, T.item_elems_mm, true);
+    S->pit_v = build_items(P->m, no_s, no_b, Cn.rp, T.rows_per_item, T.item_bytes);
   } catch (const std::bad_alloc &) {
     delete S;
     return fail(P, SABLE_ERR_OOM);
@@ -775,9 +602,9 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   const size_t o_pcv = ar.add(S->pcv.data(), vec_bytes(S->pcv));
   const size_t o_srp = ar.add(S->srp.data(), vec_bytes(S->srp));
   const size_t o_sref = ar.add(S->sref.data(), vec_bytes(S->sref));
-  size_t o_it[4][6];
-  HostItems *its[4] = {&S->it_v, &S->it_m, &S->pit_v, &S->pit_m};
-  for (int k = 0; k < 4; ++k) {
+  size_t o_it[2][6];
+  HostItems *its[2] = {&S->it_v, &S->pit_v};
+  for (int k = 0; k < 2; ++k) {
     for (int32_t q : its[k]->iseg) its[k]->pseg.push_back(S->segs[q]);
     for (int32_t q : its[k]->iblk) its[k]->pblk.push_back(S->blks[q]);
     o_it[k][4] = ar.add(its[k]->pseg.data(), vec_bytes(its[k]->pseg));
@@ -787,7 +614,7 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
     o_it[k][2] = ar.add(its[k]->iblk.data(), vec_bytes(its[k]->iblk));
   }
   char *blob = nullptr;
-  e = cudaMalloc(&blob, ar.off);
+  e = alloc_fails() ? cudaErrorMemoryAllocation : cudaMalloc(&blob, ar.off);
   if (e != cudaSuccess) {
     delete S;
     return cuda_fail(P, e);
@@ -838,7 +665,6 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   D.srp = S->srp.empty() ? nullptr : reinterpret_cast<const int32_t *>(blob + o_srp);
   D.sref = S->srp.empty() ? nullptr : reinterpret_cast<const int32_t *>(blob + o_sref);
   D.spmv = items_of(0, its[0]);
-  D.spmm = items_of(1, its[1]);
   DevHybrid &Q = P->dev_plain;
   Q = DevHybrid{};
   Q.m = D.m;
@@ -847,11 +673,9 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   Q.ci = reinterpret_cast<const int32_t *>(blob + o_pci);
   Q.cv = reinterpret_cast<const float *>(blob + o_pcv);
   Q.err = D.err;
-  Q.spmv = items_of(2, its[2]);
-  Q.spmm = items_of(3, its[3]);
+  Q.spmv = items_of(1, its[1]);
   P->stats.n_items = D.spmv.n;
   P->h_items_v = S->it_v.items;
-  P->h_items_m = S->it_m.items;
   P->h_trip = S->tc_pairs;
   P->h_fg = S->fg_pairs;
   P->h_segs = S->segs;
@@ -1106,7 +930,6 @@ sable_status sable_plan_reset(sable_plan_t P) {
   P->dev_fg = nullptr;
   P->dev_err = nullptr;
   P->h_items_v.clear();
-  P->h_items_m.clear();
   P->h_trip.clear();
   P->h_fg.clear();
   P->extractors.clear();
@@ -1209,31 +1032,6 @@ sable_status launch_spmm_rows_grouped(const DevHybrid *mats, const int64_t *row_
   else if (pn.V == 2) SABLE_GROUPED(2, 32);
   else SABLE_GROUPED(1, 32);
 #undef SABLE_GROUPED
-  if (cudaGetLastError() != cudaSuccess) {
-    (void)cudaGetLastError();
-    return SABLE_ERR_CUDA;
-  }
-  return SABLE_OK;
-}
-
-sable_status launch_spmm_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,
-                                 const float *const *Bs, float *const *Cs, int N, bool vbrc, int sm_count,
-                                 cudaStream_t_ st) {
-  if (n_items == 0) return SABLE_OK;
-  constexpr int TH = 256;
-  const bool vec = N % 4 == 0;   // B_i, C_i must then be 16-byte aligned (documented)
-  const int NT = vec ? 128 : 32;
-  const size_t smem = (size_t)rows_max * NT * 4 + ((size_t)rows_max + 1) * 4;
-  const int gy = (N + NT - 1) / NT;
-  auto go = [&](auto k) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(grid_for(k, TH, smem, n_items, sm_count), gy);
-    k<<<grid, TH, smem, st>>>(mats, items, n_items, rows_max, Bs, Cs, N);
-  };
-  if (vec && vbrc) go(spmm_grouped_kernel<TH, 4, true>);
-  else if (vbrc) go(spmm_grouped_kernel<TH, 1, true>);
-  else if (vec) go(spmm_grouped_kernel<TH, 4, false>);
-  else go(spmm_grouped_kernel<TH, 1, false>);
   if (cudaGetLastError() != cudaSuccess) {
     (void)cudaGetLastError();
     return SABLE_ERR_CUDA;

@@ -96,7 +96,7 @@ struct DevHybrid {
   const int32_t *rp = nullptr;   // CSR remainder row pointer (m + 1)
   const int32_t *ci = nullptr;   // padded by kCsrPad entries
   const float *cv = nullptr;     // padded by kCsrPad entries
-  DevItems spmv, spmm;
+  DevItems spmv;
   int32_t *err = nullptr;        // device error word (0 = ok)
 };
 
@@ -110,10 +110,8 @@ constexpr int kCsrPad = 8;
 struct Tiling {
   int32_t rows_per_item = 512;   // SpMV row tile (<= kRangeRows, multiple of 4)
   int64_t item_bytes = 48 * 1024;
-  int32_t rows_per_item_mm = 32; // SpMM row tile (<= 256, multiple of 4)
-  int64_t item_elems_mm = 4096;  // stored cells + entries per SpMM tile
   int32_t spmm_cols = 0;         // SpMM column panel per CTA: 0 = widest the operands allow, 32, 64, 128
-  int32_t spmm_depth = 4;        // SpMM: B rows in flight per warp (4 or 8; 8 with 64 or 128 columns)
+  int32_t spmm_depth = 4;        // SpMM: B rows in flight per lane group (4 or 8)
 };
 
 // Host-side extracted hybrid form and its device mirror.
@@ -156,7 +154,7 @@ struct sable_plan_s {
   sable::DevHybrid *dev_self = nullptr;// device copy of `dev` (matrix table of one entry)
   const int32_t *dev_trip = nullptr;   // (0, block, row tile) triples for the tensor-core path
   const int32_t *dev_fg = nullptr;     // (0, block, row group) triples for the FP32 block kernel
-  std::vector<sable::DevItem> h_items_v, h_items_m;   // host copies of the tile tables
+  std::vector<sable::DevItem> h_items_v;   // host copy of the SpMV tile table
   std::vector<int32_t> h_trip, h_fg;
   sable::DevHybrid dev_plain;          // whole matrix as CSR (comparison kernel)
   int32_t *dev_err = nullptr;
@@ -168,6 +166,11 @@ struct sable_plan_s {
 namespace sable {
 // host_plan.cpp
 sable_status fail(sable_plan_t p, sable_status s);
+// Allocation-failure injection (sable_debug_fail_allocations): alloc_point()
+// throws std::bad_alloc, and alloc_fails() returns true, when the countdown
+// reaches this guarded allocation; both do nothing while injection is off.
+void alloc_point();
+bool alloc_fails();
 // host_band.cpp: Algorithms 3 and 4; returns accepted segments (acceptance order)
 // as (row0, row_end, d, L, U).
 struct BandSeg { int64_t i0, i1, d, L, U, z; };
@@ -199,9 +202,6 @@ sable_status launch_spmv_grouped(const DevHybrid *mats, const DevItem *items, in
 sable_status launch_spmm_rows_grouped(const DevHybrid *mats, const int64_t *row_base, int count, int64_t rows,
                                       const float *const *Bs, float *const *Cs, int N, bool vbrc, int cols, int depth,
                                       int sm_count, cudaStream_t_ st);
-sable_status launch_spmm_grouped(const DevHybrid *mats, const DevItem *items, int n_items, int rows_max,
-                                 const float *const *Bs, float *const *Cs, int N, bool vbrc, int sm_count,
-                                 cudaStream_t_ st);
 // sable_spmv.cu
 int spmv_resident_ctas(int rows_max);   // SpMV CTAs one SM holds at this tile height
 sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const float *x, float *y,

@@ -67,9 +67,8 @@ sable_status time_op(sable_plan_t P, int op, int64_t N, const float *in, float *
 
 sable_status apply(sable_plan_t P, const sable_tiling &t, cudaStream_t st) {
   const Tiling &now = P->tiling;
-  const bool same_tables = P->uploaded && now.rows_per_item == t.spmv_rows && now.item_bytes == t.spmv_bytes &&
-                           now.rows_per_item_mm == t.spmm_rows && now.item_elems_mm == t.spmm_elems;
-  sable_status s = sable_plan_set_tiling(P, t.spmv_rows, t.spmv_bytes, t.spmm_rows, t.spmm_elems);
+  const bool same_tables = P->uploaded && now.rows_per_item == t.spmv_rows && now.item_bytes == t.spmv_bytes;
+  sable_status s = sable_plan_set_tiling(P, t.spmv_rows, t.spmv_bytes);
   if (!s) s = sable_plan_set_spmm_cols(P, t.spmm_cols);
   if (!s) s = sable_plan_set_spmm_depth(P, t.spmm_depth);
   if (!s && !same_tables) s = sable_plan_upload(P, st);   // the column panel needs no new tables
@@ -87,8 +86,6 @@ sable_status sable_plan_get_tiling(sable_plan_t P, sable_tiling *out) {
   if (!P || !out) return SABLE_ERR_INVALID;
   out->spmv_rows = P->tiling.rows_per_item;
   out->spmv_bytes = P->tiling.item_bytes;
-  out->spmm_rows = P->tiling.rows_per_item_mm;
-  out->spmm_elems = P->tiling.item_elems_mm;
   out->spmm_cols = P->tiling.spmm_cols;
   out->spmm_depth = P->tiling.spmm_depth;
   return SABLE_OK;
@@ -116,8 +113,6 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
         t.spmv_rows = it->second.spmv_rows;
         t.spmv_bytes = it->second.spmv_bytes;
       } else {
-        t.spmm_rows = it->second.spmm_rows;
-        t.spmm_elems = it->second.spmm_elems;
         t.spmm_cols = it->second.spmm_cols;
         t.spmm_depth = it->second.spmm_depth;
       }
@@ -129,7 +124,7 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
     if (spmv) {
       for (int32_t rows : {128, 256, 512, 1024})
         for (int64_t bytes : {16 << 10, 48 << 10, 160 << 10})
-          cand.push_back({rows, bytes, cur.spmm_rows, cur.spmm_elems, cur.spmm_cols, cur.spmm_depth});
+          cand.push_back({rows, bytes, cur.spmm_cols, cur.spmm_depth});
       // tiles sized for exactly 1, 2 or 3 full waves of resident CTAs
       int dev = 0, sms = 0;
       if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -138,14 +133,14 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
         const int64_t total = op == 4 ? P->stats.csr_spmv_bytes : P->stats.spmv_bytes;
         for (int64_t k = 1; k <= 3; ++k) {
           const int64_t bytes = total / (k * slots) + total / (50 * k * slots) + 64;
-          cand.push_back({kRangeRows, bytes, cur.spmm_rows, cur.spmm_elems, cur.spmm_cols, cur.spmm_depth});
+          cand.push_back({kRangeRows, bytes, cur.spmm_cols, cur.spmm_depth});
         }
       }
       (void)cudaGetLastError();
     } else {
       // one matrix's SpMM is row split: only the column panel and depth matter
-      for (const auto &cd : {std::pair<int32_t, int32_t>{128, 4}, {128, 8}, {64, 4}, {64, 8}, {32, 4}})
-        cand.push_back({cur.spmv_rows, cur.spmv_bytes, cur.spmm_rows, cur.spmm_elems, cd.first, cd.second});
+      for (const auto &cd : {std::pair<int32_t, int32_t>{128, 4}, {128, 8}, {64, 4}, {64, 8}, {32, 4}, {32, 8}})
+        cand.push_back({cur.spmv_rows, cur.spmv_bytes, cd.first, cd.second});
     }
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -1,16 +1,17 @@
-"""Tile-shape tuning of a batch: the grouped launch over many plans
-(sable_batch_*) runs every plan with its own row tiles, so the batch is tuned
-as a whole.  Each candidate tiling is set on every plan, the plans are
-uploaded again, a batch is built and its grouped launch timed with CUDA
-events (the launch replayed from a CUDA graph, as a batch is meant to be
-run); the fastest candidate is left applied.  Single plans are tuned by the
-library's own sable_autotune (Plan.autotune)."""
+"""Tiling of a batch: the grouped SpMV launch over many plans (sable_batch_*)
+runs every plan with its own row tiles, and the grouped SpMM launch uses the
+first plan's column panel and depth, so the batch is tuned as a whole.  Each
+candidate is set on every plan (SpMV tiles need a new upload), a batch is
+built and its grouped launch timed with CUDA events (replayed from a CUDA
+graph, as a batch is meant to be run); the fastest candidate is left
+applied.  Single plans are tuned by the library's own sable_autotune
+(Plan.autotune)."""
 from __future__ import annotations
 
 from . import BF16_BLOCKS, FP32, Batch
 
 SPMV_CANDIDATES = [(r, b) for r in (128, 256, 512, 1024) for b in (16 << 10, 48 << 10, 160 << 10)]
-SPMM_CANDIDATES = [(r, e) for r in (8, 16, 32, 64) for e in (1024, 4096, 16384)]
+SPMM_CANDIDATES = [(c, d) for c in (0, 32, 64, 128) for d in (4, 8)]   # (column panel, B rows in flight)
 
 
 def _time(fn, reps, stream):
@@ -43,10 +44,11 @@ def tune_batch(plans, op, ins, outs, N=0, reps=10, stream=None):
         if op == "spmv":
             t.update(spmv_rows=a, spmv_bytes=b)
         else:
-            t.update(spmm_rows=a, spmm_elems=b)
+            t.update(spmm_cols=a, spmm_depth=b)
         for P in plans:
             P.set_tiling(**t)
-            P.upload(stream)
+            if op == "spmv":
+                P.upload(stream)   # SpMV tiles are tables; the SpMM panel and depth are launch knobs
         B = Batch(plans)
         if op == "spmv":
             g = B.graph_spmv(ins, outs)
@@ -60,8 +62,9 @@ def tune_batch(plans, op, ins, outs, N=0, reps=10, stream=None):
     if op == "spmv":
         best.update(spmv_rows=a, spmv_bytes=b)
     else:
-        best.update(spmm_rows=a, spmm_elems=b)
+        best.update(spmm_cols=a, spmm_depth=b)
     for P in plans:
         P.set_tiling(**best)
-        P.upload(stream)
+        if op == "spmv":
+            P.upload(stream)
     return best, times

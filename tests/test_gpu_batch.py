@@ -104,7 +104,8 @@ def test_batch_tiling_tuner():
     Bs = [torch.from_numpy(synth.dense_operand(50 + i, A["n"], N)).cuda() for i, A in enumerate(mats)]
     Cs = [torch.empty(A["m"], N, device="cuda") for A in mats]
     bm, _ = tune.tune_batch(plans, "spmm_bf16", Bs, Cs, N=N, reps=3)
-    assert all(P.tiling()["spmm_rows"] == bm["spmm_rows"] for P in plans)
+    assert all((P.tiling()["spmm_cols"], P.tiling()["spmm_depth"]) == (bm["spmm_cols"], bm["spmm_depth"])
+               for P in plans)
     B = sable.Batch(plans)
     for y in ys:
         y.fill_(float("nan"))

@@ -84,10 +84,9 @@ def test_spmv_small(case, plan):
     P.close()
 
 
-@pytest.mark.parametrize("tiling", [dict(spmv_rows=4, spmv_bytes=64, spmm_rows=4, spmm_elems=1, spmm_cols=32),
-                                    dict(spmv_rows=1024, spmv_bytes=1 << 22, spmm_rows=256, spmm_elems=1 << 20,
-                                         spmm_depth=8),
-                                    dict(spmv_rows=36, spmv_bytes=300, spmm_rows=12, spmm_elems=100, spmm_cols=64)])
+@pytest.mark.parametrize("tiling", [dict(spmv_rows=4, spmv_bytes=64, spmm_cols=32),
+                                    dict(spmv_rows=1024, spmv_bytes=1 << 22, spmm_depth=8),
+                                    dict(spmv_rows=36, spmv_bytes=300, spmm_cols=64)])
 def test_spmv_integer_exact_any_tiling(tiling):
     rng = np.random.default_rng(42)
     m, n = 1501, 1203

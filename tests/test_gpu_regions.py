@@ -76,3 +76,38 @@ def test_update_values_on_the_device(k):
     torch.cuda.synchronize()
     assert oracle.normwise_err(yp.cpu().numpy(), oracle.spmv(A["m"], A["row"], A["col"], v2, xs)) <= 1e-5
     P.close()
+
+
+def test_injected_device_allocation_failures_return_oom():
+    """The upload's host staging and device allocation, and a batch's device
+    allocation, fail on request with SABLE_ERR_OOM; nothing is left
+    half-built and later uploads and batches work."""
+    import numpy as np
+    import synth
+    L = sable.lib()
+    A = synth.mixed_matrix(np.random.default_rng(8), 1500, 12.0)
+    spec = [(sable.VDIA, None), (sable.CSR, None)]
+    try:
+        for after in (0, 1):                       # 0: host staging, 1: device allocation
+            P = sable.plan_from(A, spec, upload=False)
+            L.sable_debug_fail_allocations(after)
+            assert L.sable_plan_upload(P.handle, None) == 2
+            L.sable_debug_fail_allocations(-1)
+            P.close()
+        P = sable.plan_from(A, spec)
+        L.sable_debug_fail_allocations(0)
+        import ctypes
+        arr = (ctypes.c_void_p * 1)(P.handle)
+        h = ctypes.c_void_p()
+        assert L.sable_batch_create(arr, 1, ctypes.byref(h)) == 2 and not h.value
+    finally:
+        L.sable_debug_fail_allocations(-1)
+    B = sable.Batch([P])
+    x = torch.from_numpy(synth.dense_operand(1, A["n"])).cuda()
+    y = torch.empty(A["m"], device="cuda")
+    B.spmv([x], [y])
+    torch.cuda.synchronize()
+    ref = oracle.spmv(A["m"], A["row"], A["col"], A["val"], x.cpu().numpy())
+    assert oracle.normwise_err(y.cpu().numpy(), ref) <= 1e-5
+    B.close()
+    P.close()

@@ -12,7 +12,6 @@ import synth
 pytestmark = pytest.mark.gpu
 
 SPMV_ROWS, SPMV_BYTES = {128, 256, 512, 1024}, {16 << 10, 48 << 10, 160 << 10}
-SPMM_ROWS, SPMM_ELEMS = {8, 16, 32, 64}, {1024, 4096, 16384}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -42,8 +41,7 @@ def test_autotune_spmv_and_spmm():
     refm = oracle.spmm(A["m"], A["row"], A["col"], A["val"], Bs)
     for op, tol in ((sable.TUNE_SPMM_FP32, 1e-5), (sable.TUNE_SPMM_BF16, 2e-2)):
         tm, msm = P.autotune(op, B, C, reps=3)
-        assert tm["spmm_rows"] in SPMM_ROWS and tm["spmm_elems"] in SPMM_ELEMS
-        assert (tm["spmm_cols"], tm["spmm_depth"]) in ((128, 4), (128, 8), (64, 4), (64, 8), (32, 4))
+        assert (tm["spmm_cols"], tm["spmm_depth"]) in ((128, 4), (128, 8), (64, 4), (64, 8), (32, 4), (32, 8))
         assert msm > 0
         assert (tm["spmv_rows"], tm["spmv_bytes"]) == (t["spmv_rows"], t["spmv_bytes"])   # SpMV choice kept
         C.fill_(float("nan"))

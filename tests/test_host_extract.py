@@ -224,3 +224,35 @@ def test_wait_limit_bounds_checked_on_the_host():
     sable.set_wait_limit(123456)
     assert sable.wait_limit() == 123456
     sable.set_wait_limit(old)
+
+
+def test_injected_allocation_failures_return_oom():
+    """Host-side allocation-failure injection: the failing call returns
+    SABLE_ERR_OOM, a plan that failed keeps it as its status, and the library
+    works normally once injection is off."""
+    L = sable.lib()
+    rng = np.random.default_rng(3)
+    A = synth.assemble(rng, 300, 300, bands=[(0, 0, 300), (1, 0, 300)], n_scatter=500)
+    row = np.ascontiguousarray(A["row"], np.int32)
+    col = np.ascontiguousarray(A["col"], np.int32)
+    val = np.ascontiguousarray(A["val"], np.float32)
+    import ctypes
+    h = ctypes.c_void_p()
+    try:
+        L.sable_debug_fail_allocations(0)          # the next guarded allocation fails: plan creation
+        st = L.sable_plan_create(300, 300, row.size, row.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                 ctypes.byref(h))
+        assert st == 2 and not h.value             # SABLE_ERR_OOM, no plan handed out
+        L.sable_debug_fail_allocations(0)          # creation passes after the reset below
+        L.sable_debug_fail_allocations(-1)
+        P = sable.Plan(300, 300, row, col, val)
+        P.add_extractor(sable.VDIA, a_min=50, l_seg=8).add_extractor(sable.CSR)
+        L.sable_debug_fail_allocations(0)          # now extraction's allocation fails
+        assert L.sable_extract(P.handle) == 2
+        assert L.sable_plan_status(P.handle) == 2  # sticky
+        P.close()
+    finally:
+        L.sable_debug_fail_allocations(-1)
+    P = sable.plan_from(A, [(sable.VDIA, dict(a_min=50, l_seg=8)), (sable.CSR, None)], upload=False)
+    assert P.info()["nnz_vdia"] > 0
+    P.close()

@@ -72,7 +72,12 @@ typedef enum { SABLE_FP32 = 0, SABLE_BF16_BLOCKS = 1, SABLE_FP32_SPLIT = 2 } sab
  *   coverage_min share of entries blocks must cover, else none are kept (0.08)
  *   max_span     cap on FindBlock's outer span (Algorithm 2)
  *   tile         candidate-region pre-pass cell size; 0 runs Algorithm 1 on
- *                the whole matrix */
+ *                the whole matrix
+ *   passes       VDIA: runs of Algorithm 3, each over the residual the previous
+ *                one left and with its own row mask, so a row may carry bands
+ *                of several passes at different offsets (multi-ribbon VDIA; a
+ *                segment's diagonal set is its own, Section 4.2.1); added as
+ *                that many consecutive band stages; 1..8, default 1 */
 typedef struct {
   double delta;
   int64_t a_min;
@@ -83,6 +88,7 @@ typedef struct {
   double coverage_min;
   int32_t max_span;
   int32_t tile;
+  int32_t passes;
 } sable_extract_params;
 
 /* Summary of an extracted plan.  Byte counts are the algorithmic bytes one

@@ -23,6 +23,15 @@ same readings, written independently):
   between; the narrower resulting ribbon wins (below on a tie), and is taken
   only when its density stays >= delta and the side's extent stays <= w_max.
   k_i is the number of entries in the final ribbon [d - l_i, d + u_i].
+* Multi-ribbon VDIA (passes > 1): Algorithm 3 runs `passes` times, each
+  pass over the residual the previous one left and with its own row mask
+  (Algorithm 3's used[] starts false), so a row may carry ribbons of several
+  passes at different offsets, e.g. a main band and a far band whose rows a
+  first pass masked.  ``merge_segments`` gives the VDIA layout of such a
+  partition (Section 4.2.1: each segment carries its own list of diagonal
+  offsets): the row ranges are cut at every segment boundary and each piece
+  covered by the same segments becomes one segment whose offsets are the
+  sorted union of theirs.
 * GrowSegments (Algorithm 4), literally; "nnz at row j" counts row j's
   entries inside the current ribbon [d - L, d + U].  Segment area is
   (L + U + 1) x rows, cells outside [0, ncols) included (stored as zeros).
@@ -71,6 +80,7 @@ class Params:
     coverage_min: float = 0.08
     max_span: int = 512
     tile: int = 8
+    passes: int = 1         # VDIA: runs of Algorithm 3 over the shrinking residual
 
 
 def default_params(kind: int) -> Params:
@@ -436,12 +446,16 @@ def run_plan(m: int, n: int, row, col, val, extractors: Sequence[Tuple[int, Opti
         if kind == CSR:
             owner[ids] = CSR
         elif kind == VDIA:
-            for (i0, j, d, L, U, z) in extract_bands(R, p):
-                ex.segments.append((i0, j - i0, d - L, L + U + 1))
-                for r in range(i0, j):
-                    for c, e in zip(R.rowlist[r], R.rowids[r]):
-                        if d - L <= c - r <= d + U:
-                            owner[e] = VDIA
+            for ps in range(p.passes):
+                if ps > 0:   # the next pass sees the residual this one left
+                    ids = np.nonzero(owner < 0)[0]
+                    R = Residual(m, n, rows[ids], cols[ids], ids)
+                for (i0, j, d, L, U, z) in extract_bands(R, p):
+                    ex.segments.append((i0, j - i0, d - L, L + U + 1))
+                    for r in range(i0, j):
+                        for c, e in zip(R.rowlist[r], R.rowids[r]):
+                            if d - L <= c - r <= d + U:
+                                owner[e] = VDIA
         elif kind == VBR:
             for (r0, r1, c0, c1, z) in partition_blocks(R, p):
                 ex.blocks.append((r0, r1 - r0, c0, c1 - c0))
@@ -456,6 +470,25 @@ def run_plan(m: int, n: int, row, col, val, extractors: Sequence[Tuple[int, Opti
     ex.segments.sort()
     ex.blocks.sort()
     return ex
+
+
+def merge_segments(segments):
+    """VDIA segments of several passes, (row_start, nrows, lowest offset,
+    ndiags) each, as one segment list with per-segment offset sets: the rows
+    are cut at every segment start and end, and each maximal row range that
+    the same segments cover becomes (row_start, nrows, sorted union of their
+    offsets).  Rows no segment covers are left out."""
+    cuts = sorted({r for (r0, nr, _, _) in segments for r in (r0, r0 + nr)})
+    out = []
+    for a, b in zip(cuts, cuts[1:]):
+        offs = sorted({o for (r0, nr, lo, nd) in segments if r0 <= a and b <= r0 + nr for o in range(lo, lo + nd)})
+        if not offs:
+            continue
+        if out and out[-1][0] + out[-1][1] == a and out[-1][2] == tuple(offs):
+            out[-1] = (out[-1][0], out[-1][1] + b - a, out[-1][2])   # same set continues
+        else:
+            out.append((a, b - a, tuple(offs)))
+    return out
 
 
 def check_partition(ex: Extraction, vdia_cells, vbr_cells, csr_entries) -> None:

@@ -59,7 +59,7 @@ class Params(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("a_min", ctypes.c_int64), ("l_seg", ctypes.c_int32),
                 ("w_max", ctypes.c_int32), ("d_max", ctypes.c_int64), ("count_min", ctypes.c_int64),
                 ("coverage_min", ctypes.c_double), ("max_span", ctypes.c_int32),
-                ("tile", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("passes", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -225,7 +225,7 @@ class Plan:
         for k, v in kw.items():
             setattr(p, k, v)
         _check(lib().sable_plan_add_extractor(self._h, kind, ctypes.byref(p)), "add_extractor")
-        self._stages.append(kind)
+        self._stages.extend([kind] * max(1, p.passes))   # a multi-pass band extractor adds one stage per pass
         return self
 
     def add_regions(self, kind: int, regions):

@@ -93,6 +93,7 @@ void sable_default_params(sable_extractor kind, sable_extract_params *o) {
   o->coverage_min = 0.08;
   o->max_span = 512;
   o->tile = 8;
+  o->passes = 1;
 }
 
 sable_status sable_plan_create(int64_t m, int64_t n, int64_t nnz, const int32_t *row,
@@ -163,11 +164,20 @@ sable_status sable_plan_add_extractor(sable_plan_t P, sable_extractor kind,
   if (params) p = *params;
   if (!(p.delta > 0.0 && p.delta <= 1.0) || p.a_min < 1 || p.l_seg < 1 || p.w_max < 0 || p.w_max > 512 ||
       p.d_max < 0 || p.count_min < 0 || !(p.coverage_min >= 0.0) || p.max_span < 1 ||
-      p.tile < 0)
+      p.tile < 0 || p.passes < 1 || p.passes > 8 || (kind != SABLE_X_VDIA && p.passes != 1))
     return SABLE_ERR_INVALID;
-  P->extractors.push_back({kind, p});
-  P->stage_regions.emplace_back();
-  P->stage_fixed.push_back(0);
+  // multi-ribbon VDIA: one band stage per pass, each over the residual of the last
+  const int passes = p.passes;
+  p.passes = 1;
+  try {
+    for (int k = 0; k < passes; ++k) {
+      P->extractors.push_back({kind, p});
+      P->stage_regions.emplace_back();
+      P->stage_fixed.push_back(0);
+    }
+  } catch (const std::bad_alloc &) {
+    return fail(P, SABLE_ERR_OOM);
+  }
   return SABLE_OK;
 }
 

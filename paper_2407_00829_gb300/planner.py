@@ -113,16 +113,24 @@ def matrix_features(A, device="cuda") -> np.ndarray:
     return features(A["m"], A["n"], row, col).cpu().numpy()
 
 
-def _time_ms(fn, reps=20, warm=3, rounds=3):
-    """Mean device ms of one launch over `reps` back-to-back launches, best of
-    `rounds` (events around each launch would also time the host's launch
-    gaps, a large and noisy share of a tens-of-microseconds SpMV)."""
+def _time_ms(fn, warm=3, rounds=5, min_ms=1.5, reps=None):
+    """Mean device ms of one launch over back-to-back launches, best of
+    `rounds`; each round runs enough launches to last about min_ms (events
+    around each launch would also time the host's launch gaps, a large and
+    noisy share of a tens-of-microseconds SpMV, and short rounds leave the
+    minimum noisy)."""
     import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
     for _ in range(warm):
         fn()
+    b.record()
+    torch.cuda.synchronize()
+    if reps is None:
+        est = max(a.elapsed_time(b) / warm, 1e-3)
+        reps = int(min(2000, max(10, math.ceil(min_ms / est))))
     best = float("inf")
     for _ in range(rounds):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(reps):
             fn()
@@ -132,19 +140,29 @@ def _time_ms(fn, reps=20, warm=3, rounds=3):
     return best
 
 
-def time_plan(P, A, x, y, B, C):
+def _op_fn(P, N, x, y, B, C):
+    return (lambda: P.spmv(x, y)) if N == 0 else (lambda: P.spmm(B, C, BF16_BLOCKS))
+
+
+def time_plan(P, A, x, y, B, C, rounds=5):
     """Device ms of each op in OPS for one uploaded plan."""
-    out = []
-    for _, N in OPS:
-        if N == 0:
-            out.append(_time_ms(lambda: P.spmv(x, y)))
-        else:
-            out.append(_time_ms(lambda: P.spmm(B, C, BF16_BLOCKS)))
-    return out
+    return [_time_ms(_op_fn(P, N, x, y, B, C), rounds=rounds) for _, N in OPS]
 
 
-def build_plans(A, tables=None, workers=9):
-    """All candidate plans of A, uploaded: from region tables when given."""
+def time_candidates(plans, A, x, y, B, C, top=3):
+    """ms of every candidate x op; the `top` fastest of each op are then timed
+    again with twice the rounds and keep their best, so that the exhaustive
+    planner's minimum is not a noise low of one candidate."""
+    t = np.array([time_plan(P, A, x, y, B, C) for P in plans], np.float64)
+    for o, (_, N) in enumerate(OPS):
+        for c in np.argsort(t[:, o])[:top]:
+            t[c, o] = min(t[c, o], _time_ms(_op_fn(plans[c], N, x, y, B, C), rounds=10))
+    return t
+
+
+def build_plans(A, tables=None, workers=9, upload=True):
+    """All candidate plans of A (uploaded unless upload=False): from region
+    tables when given."""
     def one(c):
         name, spec = CANDIDATES[c]
         if tables is None:
@@ -152,8 +170,9 @@ def build_plans(A, tables=None, workers=9):
         return _new_plan(A).add_stages(tables[name]).extract()
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         plans = list(ex.map(one, range(len(CANDIDATES))))
-    for P in plans:
-        P.upload()
+    if upload:
+        for P in plans:
+            P.upload()
     return plans
 
 
@@ -178,11 +197,13 @@ def exhaustive(A, op=0, tables=None):
     return int(np.argmin(t)), t, time.perf_counter() - t0
 
 
-def collect(indices, seed=1005, rows=(100_000, 1_000_000), table_dir=None, log=None):
-    """Features and timings (candidates x ops) of the given planner matrices."""
+def collect(indices, seed=1005, rows=(100_000, 1_000_000), table_dir=None, log=None, ahead=3):
+    """Features and timings (candidates x ops) of the given planner matrices.
+    Host threads generate the next `ahead` matrices and rebuild their
+    candidate plans while the device times the current one."""
     import synth
-    feats, times, meta = [], [], []
-    for i in indices:
+
+    def prepare(i):
         A = synth.planner_set_matrix(i, seed=seed, rows=rows)
         tables, from_tables = None, 0
         if table_dir:
@@ -191,10 +212,22 @@ def collect(indices, seed=1005, rows=(100_000, 1_000_000), table_dir=None, log=N
                 from_tables = 1
             else:   # another structure than the tables were made for: extract here
                 tables = None
+        return A, build_plans(A, tables, upload=False), from_tables
+
+    feats, times, meta = [], [], []
+    indices = list(indices)
+    pool = cf.ThreadPoolExecutor(max_workers=ahead)
+    futs = [pool.submit(prepare, i) for i in indices[:ahead]]
+    for k, i in enumerate(indices):
+        A, plans, from_tables = futs[k].result()
+        futs[k] = None
+        if k + ahead < len(indices):
+            futs.append(pool.submit(prepare, indices[k + ahead]))
         f = matrix_features(A)
-        plans = build_plans(A, tables)
+        for P in plans:
+            P.upload()
         x, y, B, C = _operands(A, i)
-        t = [time_plan(P, A, x, y, B, C) for P in plans]
+        t = time_candidates(plans, A, x, y, B, C).tolist()
         for P in plans:
             P.close()
         feats.append(f)

@@ -256,3 +256,39 @@ def test_injected_allocation_failures_return_oom():
     P = sable.plan_from(A, [(sable.VDIA, dict(a_min=50, l_seg=8)), (sable.CSR, None)], upload=False)
     assert P.info()["nnz_vdia"] > 0
     P.close()
+
+
+@pytest.mark.parametrize("passes", [2, 3])
+def test_multi_pass_bands_match_oracle(passes):
+    """Multi-ribbon VDIA: the library's band stages per pass give exactly the
+    oracle's segments, values and remainder; the far band that one pass sends
+    to CSR comes back as a second-pass segment, and the plan rebuilt from its
+    region table is identical."""
+    A = synth.assemble(np.random.default_rng(4), 200, 260, bands=[(-1, 0, 200), (0, 0, 200), (1, 0, 200),
+                                                                  (50, 0, 200)], values="int")
+    ex = _compare(A, [(sable.VDIA, dict(delta=0.75, a_min=100, l_seg=16, passes=passes)), (sable.CSR, None)])
+    assert sorted(ex.segments) == [(0, 200, -1, 3), (0, 200, 50, 1)]
+    rng = np.random.default_rng(11)
+    m = 3000
+    B = synth.assemble(rng, m, m, bands=[(o, int(rng.integers(0, 800)), int(rng.integers(1500, 2200)))
+                                         for o in (-2, -1, 0, 1, 2, -300, -299, 300, 301)], n_scatter=4000)
+    spec = [(sable.VDIA, dict(delta=0.75, a_min=256, l_seg=16, passes=passes)), (sable.CSR, None)]
+    ex = _compare(B, spec)
+    one = ox.run_plan(m, m, B["row"], B["col"], B["val"], [(ox.VDIA, ox.Params(delta=0.75, a_min=256, l_seg=16)),
+                                                          (ox.CSR, None)])
+    assert np.sum(ex.owner == ox.CSR) < np.sum(one.owner == ox.CSR)   # fewer entries left to CSR
+    P = sable.plan_from(B, spec, upload=False)
+    Q = sable.Plan(m, m, B["row"], B["col"], B["val"]).add_stages(P.region_table()).extract()
+    assert np.array_equal(P.segments(), Q.segments()) and np.array_equal(P.vdia_values(), Q.vdia_values())
+    assert P.region_stages()[0].max() == passes - 1
+    P.close()
+    Q.close()
+
+
+def test_passes_rejected_outside_range_and_for_other_kinds():
+    A = synth.assemble(np.random.default_rng(1), 50, 50, n_scatter=100)
+    P = sable.Plan(A["m"], A["n"], A["row"], A["col"], A["val"])
+    for kind, passes in ((sable.VDIA, 0), (sable.VDIA, 9), (sable.VBR, 2), (sable.CSR, 2)):
+        with pytest.raises(sable.SableError):
+            P.add_extractor(kind, passes=passes)
+    P.close()

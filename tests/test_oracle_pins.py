@@ -435,3 +435,47 @@ def test_row_order_spmv_is_identical_to_the_coo_loop(threads):
     assert np.array_equal(y.view(np.uint64), ref.view(np.uint64))
     assert np.all(np.diff(ro.rp) >= 0) and ro.rp[-1] == nnz
     assert np.all(np.diff(row[ro.perm].astype(np.int64)) >= 0)      # grouped by row
+
+
+def test_merge_segments_by_hand():
+    # rows 0..9 carry offsets -1..1 (one pass), rows 5..14 offsets 40, 41
+    # (another): three row ranges, [0,5) {-1,0,1}, [5,10) {-1,0,1,40,41},
+    # [10,15) {40,41}; a third segment continuing the last set merges into it
+    segs = [(0, 10, -1, 3), (5, 10, 40, 2), (15, 5, 40, 2)]
+    assert ox.merge_segments(segs) == [(0, 5, (-1, 0, 1)), (5, 5, (-1, 0, 1, 40, 41)), (10, 10, (40, 41))]
+    assert ox.merge_segments([(3, 4, 2, 1)]) == [(3, 4, (2,))]
+    assert ox.merge_segments([]) == []
+
+
+def test_second_band_pass_claims_far_band_on_masked_rows():
+    # a main band {-1, 0, 1} and a far band {+50} on the same 200 rows.  One
+    # pass of Algorithm 3: the first candidate (offset -1, ties by offset)
+    # grows to the ribbon [-1, 1] on every row (the far band is 49 zero cells
+    # away: density 4/52 < delta) and masks all rows, so offset 50 finds no
+    # unmasked row and goes to CSR.  A second pass over that residual finds
+    # the far band alone: one segment, offset 50.  The merged layout is one
+    # segment with idiag [-1, 0, 1, 50] (Section 4.2.1), arrays by hand.
+    m, n = 200, 260
+    A = synth.assemble(np.random.default_rng(4), m, n, bands=[(-1, 0, m), (0, 0, m), (1, 0, m), (50, 0, m)],
+                       values="int")
+    one = ox.run_plan(m, n, A["row"], A["col"], A["val"],
+                      [(ox.VDIA, ox.Params(delta=0.75, a_min=100, l_seg=16)), (ox.CSR, None)])
+    assert one.segments == [(0, 200, -1, 3)]
+    far = (one.cols - one.rows) == 50
+    assert np.all(one.owner[far] == ox.CSR) and np.all(one.owner[~far] == ox.VDIA)
+    two = ox.run_plan(m, n, A["row"], A["col"], A["val"],
+                      [(ox.VDIA, ox.Params(delta=0.75, a_min=100, l_seg=16, passes=2)), (ox.CSR, None)])
+    assert sorted(two.segments) == [(0, 200, -1, 3), (0, 200, 50, 1)]
+    assert np.all(two.owner == ox.VDIA)
+    merged = ox.merge_segments(two.segments)
+    assert merged == [(0, 200, (-1, 0, 1, 50))]
+    entries = {(int(i), int(j)): float(v) for i, j, v in zip(two.rows, two.cols, two.vals)}
+    arr = of.vdia_arrays(entries, n, merged)
+    assert arr["idiag"] == [-1, 0, 1, 50] and arr["seg_ndiags"] == [4] and arr["seg_nrows"] == [200]
+    assert arr["seg_val_ptr"] == [0] and arr["seg_idiag_ptr"] == [0]
+    val = arr["val"]
+    assert len(val) == 800 and val[0] == 0.0                      # row 0 has no column -1
+    for k, off in enumerate((-1, 0, 1, 50)):
+        for r in range(m):
+            c = r + off
+            assert val[200 * k + r] == (entries.get((r, c), 0.0) if 0 <= c < n else 0.0)

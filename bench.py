@@ -484,6 +484,15 @@ def run_batch(args):
     res["spmm_fp32_per_matrix_ms"] = timed(
         lambda: [P.spmm(b, c, sable.FP32, stream) for P, b, c in zip(plans, Bs, Cs)], 3)
     assert B.device_error() == 0
+    # SpMM algorithmic bytes of the batch (every stored value and index once,
+    # B once, C once; BF16 block cells 2 bytes) and its HBM fraction
+    peak, peak_src = _peaks()
+    mbytes = {cb: sum(4 * i["vdia_cells"] + cb * i["vbr_cells"] + 8 * i["nnz_csr"] + 4 * (i["m"] + 1) +
+                      32 * (i["n_segments"] + i["n_blocks"]) + 4 * i["n"] * N + 4 * i["m"] * N for i in infos)
+              for cb in (2, 4)}
+    spmm_roof = {name: {"bytes": mbytes[cb], "GB/s": mbytes[cb] / (res[f"spmm_{name}_graph_ms"] * 1e-3) / 1e9,
+                        "frac_hbm": mbytes[cb] / (res[f"spmm_{name}_graph_ms"] * 1e-3) / 1e9 / peak}
+                 for name, cb in (("fp32", 4), ("bf16_blocks", 2))}
     ms = res["spmv_graph_ms"]
     line = {"metric": METRIC, "value": vbytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": k,
             "warmup": 3, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -496,6 +505,8 @@ def run_batch(args):
             "spmv_GB/s": vbytes / (ms * 1e-3) / 1e9,
             "spmm_fp32_GFLOP/s": 2.0 * nnz * N / (res["spmm_fp32_graph_ms"] * 1e-3) / 1e9,
             "spmm_bf16_GFLOP/s": 2.0 * nnz * N / (res["spmm_bf16_blocks_graph_ms"] * 1e-3) / 1e9,
+            "spmm_roofline": dict(spmm_roof, peak=peak, peak_source=peak_src, bound="hbm"),
+            "spmv_frac_hbm": vbytes / (ms * 1e-3) / 1e9 / peak,
             "times_ms": res, "autotune": autotune, "gpu_launches": 1}
     print(json.dumps(line), flush=True)
     gv.close()
@@ -676,6 +687,15 @@ def main():
             hybrid(i % reps)
         torch.cuda.synchronize(dev)
     ms = timed(hybrid, args.steps)
+    # the paper's timing method beside it (Section 5: 30 invocations of 30
+    # back-to-back iterations, outliers filtered by deciles, mean reported)
+    inv = []
+    for _ in range(30):
+        inv.append(timed(hybrid, 30))
+    inv_sorted = sorted(inv)
+    kept = inv_sorted[3:-3]
+    paper_method = {"invocations": 30, "iterations": 30, "decile_filtered_mean_ms": statistics.mean(kept),
+                    "median_ms": statistics.median(inv), "min_ms": inv_sorted[0], "max_ms": inv_sorted[-1]}
     clocks = clk.stop()
     # the comparison point: its best of the default tiling and its own tuned tiling
     ms_plain = min(ms_plain_tuned, ms_plain_default_tiling)
@@ -754,6 +774,42 @@ def main():
     e1.record(stream)
     barrier()
     ms_e2e = e0.elapsed_time(e1) / k_e2e
+    # the same per call on one stream, nothing overlapped: copy x in, SpMV, copy y out
+    k_ser = min(args.steps, 200)
+    barrier()
+    e0.record(stream)
+    for i in range(k_ser):
+        xs[i % reps].copy_(xh, non_blocking=True)
+        plans[i % reps].spmv(xs[i % reps], ys[i % reps], stream)
+        yh.copy_(ys[i % reps], non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ms_e2e_serial = e0.elapsed_time(e1) / k_ser
+
+    # multi-ribbon VDIA beside the one-pass plan (three band passes: the far
+    # bands that row masking sends to CSR come back as second- and third-pass
+    # segments), same rotation, timed the same way
+    multi = None
+    if args.workload == "spmv1m":
+        spec3 = [(sable.VDIA, dict(passes=3))] + [(k, None) for k in kinds[1:]]
+        mplans = [sable.plan_from(A, spec3) for _ in range(reps)]
+        for P in mplans:
+            P.set_tiling(**tuned)
+            P.upload(stream)
+        minfo = mplans[0].info()
+
+        def mhybrid(i):
+            mplans[i].spmv(xs[i], ys[i], stream)
+
+        for i in range(5):
+            mhybrid(i % reps)
+        ms_multi = timed(mhybrid, min(args.steps, 500))
+        multi = {"extractors": "VDIA (3 passes) + CSR", "ms_per_step": ms_multi, "nnz_vdia": minfo["nnz_vdia"],
+                 "nnz_csr": minfo["nnz_csr"], "segments": minfo["n_segments"], "bytes_per_step": minfo["spmv_bytes"],
+                 "GB/s": minfo["spmv_bytes"] / (ms_multi * 1e-3) / 1e9,
+                 "vs_one_pass_time": ms / ms_multi, "vs_plain_csr": min(ms_plain, cus_ms or ms_plain) / ms_multi}
+        for P in mplans:
+            P.close()
     spmm, spmm_check = None, None
     if not args.no_spmm and ws == 1:
         peak_hbm, _src = _peaks()
@@ -825,12 +881,18 @@ def main():
                               "GB/s_own_bytes": info["csr_spmv_bytes"] / (cus_ms * 1e-3) / 1e9}
                              if cus_ms else None),
             "vs_plain_csr": min(ms_plain, cus_ms or ms_plain) / ms,
+            "vs_plain_csr_what": "the faster of the library's plain CSR kernel (best tiling) and cuSPARSE CSR "
+                                 "(int32 indices), over the hybrid's time",
             "err_vs_oracle": err,
             "e2e": {"value": nbytes * ws / (ms_e2e * 1e-3) / 1e9, "unit": "GB/s",
                     "h2d_bytes_per_step": 4 * info["n"], "d2h_bytes_per_step": 4 * info["m"],
                     "ms_per_step": ms_e2e, "steps": k_e2e,
                     "how": "pinned host x -> device, sable_spmv, y -> pinned host every step; "
-                           "consecutive steps overlap on three streams (copy in, SpMV, copy out)"},
+                           "consecutive steps overlap on three streams (copy in, SpMV, copy out)",
+                    "serial_ms_per_call": ms_e2e_serial,
+                    "serial_GB/s": nbytes * ws / (ms_e2e_serial * 1e-3) / 1e9},
+            "paper_method": paper_method,
+            "multi_ribbon": multi,
             "spmm": spmm,
             "autotune": autotune,
             "reuse": reuse,

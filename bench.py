@@ -248,6 +248,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def inspector_compare(sable, A, spec):
+    """The same extraction with the host inspector and with the device
+    inspector (the extractors' counting steps on the GPU), outside any timed
+    region: wall time of each (COO ingest included, no upload) and whether
+    the two region tables, values and remainders are identical."""
+    t0 = time.perf_counter()
+    H = sable.plan_from(A, spec, upload=False)
+    t_host = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    D = sable.plan_from(A, spec, upload=False, inspector=sable.INSPECT_DEVICE)
+    t_dev = time.perf_counter() - t0
+    same = (np.array_equal(H.segments(), D.segments()) and np.array_equal(H.blocks(), D.blocks()) and
+            np.array_equal(H.vdia_values(), D.vdia_values()) and np.array_equal(H.vbr_values(), D.vbr_values()) and
+            all(np.array_equal(a, b) for a, b in zip(H.csr(), D.csr())) and H.info() == D.info())
+    H.close()
+    D.close()
+    return {"host_extract_s": round(t_host, 3), "device_extract_s": round(t_dev, 3), "identical": bool(same),
+            "what": "plan create + extract of the same stages; device: M[d], FitRibbon and pre-pass cell "
+                    "counts on the GPU (integer), the rest on the host"}
+
+
 def spmm_section(sable, torch, dev, stream, steps, timed, peak):
     """SpMM C = A B on the 200k x 200k blocks + scatter workload, N = 128:
     hybrid VBR+CSR in FP32 and with BF16 blocks on the tensor cores, against
@@ -272,7 +293,8 @@ def spmm_section(sable, torch, dev, stream, steps, timed, peak):
     out = {"workload": "spmm-vbr+csr-200k: 200,000^2, blocks side U{16..256} density 0.8 on disjoint "
                        "rows/cols (~40% of entries), uniform scatter, N=128, U[-1,1]",
            "nnz": info["nnz"], "nnz_vbr": info["nnz_vbr"], "blocks": info["n_blocks"], "N": N,
-           "extract_s": round(t_ex, 2), "steps": k}
+           "extract_s": round(t_ex, 2), "steps": k,
+           "inspector": inspector_compare(sable, A, [(sable.VBR, dict(a_min=256)), (sable.CSR, None)])}
     res = {}
     variants = (("fp32", lambda i: P.spmm(B, C, sable.FP32, stream), 4),
                 ("fp32_split", lambda i: P.spmm(B, C, sable.FP32_SPLIT, stream), 6),
@@ -618,6 +640,7 @@ def main():
     Q.close()
     reuse = {"extract_and_upload_s": round(t_extract, 3), "rebuild_from_region_table_s": round(t_rebuild, 3),
              "update_values_s": round(t_update, 3)}
+    inspector = inspector_compare(sable, A, [(k, None) for k in kinds])
     xs = [torch.from_numpy(x_np).to(dev) for _ in range(reps)]
     ys = [torch.empty(A["m"], device=dev) for _ in range(reps)]
     stream = torch.cuda.current_stream(dev)
@@ -896,6 +919,7 @@ def main():
             "spmm": spmm,
             "autotune": autotune,
             "reuse": reuse,
+            "inspector": inspector,
             "gpu_launches": args.steps,
             "clocks": clocks,
         }

@@ -141,11 +141,32 @@ sable_status sable_plan_add_extractor(sable_plan_t plan, sable_extractor kind,
 sable_status sable_plan_add_regions(sable_plan_t plan, sable_extractor kind, const int64_t *regions,
                                     int64_t count);
 
+/* Where sable_extract runs the extractors' counting steps (the inspector).
+ * SABLE_INSPECT_HOST (default): everything on the host.  SABLE_INSPECT_DEVICE:
+ * on the current CUDA device, integer arithmetic only, for each band stage the
+ * diagonal histogram M[d] of Algorithm 3 and FitRibbon (Section 4.2) of every
+ * row for every candidate offset, and for each block stage with tile > 0 the
+ * entry counts of the candidate-region pre-pass's cells; candidate order,
+ * GrowSegments (Algorithm 4), acceptance, FindBlock (Algorithm 2) and Trim
+ * stay on the host.  Both give the same regions, entry for entry (each FP64
+ * density test of the host becomes an integer threshold the host computes
+ * with the same FP64 expression). */
+typedef enum { SABLE_INSPECT_HOST = 0, SABLE_INSPECT_DEVICE = 1 } sable_inspector;
+
+/* Choose the inspector of a plan's sable_extract.  Errors: SABLE_ERR_ORDER
+ * after sable_extract; SABLE_ERR_INVALID for another value. */
+sable_status sable_plan_set_inspector(sable_plan_t plan, sable_inspector where);
+
 /* Run the extractors in order over the residual, check that the residual is
  * empty and that the regions partition the entries exactly, and build the
- * host tables (Section 3, "Extract"/"Dispatch", Section 3.4).  Host only: no
- * CUDA call.  Errors: SABLE_ERR_INCOMPLETE if entries are left unclaimed;
- * SABLE_ERR_ORDER if called twice. */
+ * host tables (Section 3, "Extract"/"Dispatch", Section 3.4).  With the host
+ * inspector no CUDA call is made; with the device inspector each searching
+ * band or block stage copies its residual CSR to the current device and works
+ * on a stream of its own, synchronously, freeing what it allocated before it
+ * returns.  Errors: SABLE_ERR_INCOMPLETE if entries are left unclaimed;
+ * SABLE_ERR_ORDER if called twice; device inspector: SABLE_ERR_UNSUPPORTED
+ * (nothing done, not sticky) for a block stage with tile > 64, SABLE_ERR_CUDA
+ * (no device, or a CUDA call failed) and SABLE_ERR_OOM. */
 sable_status sable_extract(sable_plan_t plan);
 
 /* Copy the plan's tables to the current CUDA device (asynchronously on

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsable.so")
 
 VDIA, VBR, CSR = 0, 1, 2
 FP32, BF16_BLOCKS, FP32_SPLIT = 0, 1, 2
+INSPECT_HOST, INSPECT_DEVICE = 0, 1
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime error",
           4: "incomplete plan", 5: "call out of order", 6: "device wait timed out",
@@ -39,6 +40,7 @@ EXPORTED = [
     "sable_autotune_cache_clear", "sable_plan_set_spmm_cols", "sable_plan_update_values",
     "sable_plan_set_spmm_depth", "sable_plan_device_error", "sable_probe_bulk_gather", "sable_set_wait_limit",
     "sable_get_wait_limit", "sable_probe_wait_limit", "sable_debug_fail_allocations",
+    "sable_plan_set_inspector",
 ]
 
 NFEAT = 24
@@ -85,6 +87,7 @@ def lib():
             "sable_plan_create": ([i64, i64, i64, p, p, p, p], i32),
             "sable_plan_add_extractor": ([p, i32, p], i32),
             "sable_extract": ([p], i32),
+            "sable_plan_set_inspector": ([p, i32], i32),
             "sable_plan_upload": ([p, p], i32),
             "sable_spmv": ([p, p, p, p], i32),
             "sable_csr_spmv": ([p, p, p, p], i32),
@@ -281,6 +284,12 @@ class Plan:
                 self.add_extractor(CSR)
             else:
                 self.add_regions(kind, regions)
+        return self
+
+    def set_inspector(self, where: int):
+        """INSPECT_HOST (default) or INSPECT_DEVICE: where sable_extract runs the
+        extractors' counting steps (same regions either way)."""
+        _check(lib().sable_plan_set_inspector(self._h, where), "sable_plan_set_inspector")
         return self
 
     def extract(self):
@@ -605,12 +614,15 @@ class Mlp:
                                     self.step, lr, beta1, beta2, eps, _stream_handle(stream)), "sable_mlp_adam")
 
 
-def plan_from(A: dict, extractors, tiling: Optional[dict] = None, upload: bool = True, stream=None) -> Plan:
+def plan_from(A: dict, extractors, tiling: Optional[dict] = None, upload: bool = True, stream=None,
+              inspector: int = INSPECT_HOST) -> Plan:
     """Create, extract and (optionally) upload a plan for a COO dict
     {m, n, row, col, val}; ``extractors`` is a list of (kind, params-dict or None)."""
     P = Plan(A["m"], A["n"], A["row"], A["col"], A["val"])
     for kind, kw in extractors:
         P.add_extractor(kind, **(kw or {}))
+    if inspector != INSPECT_HOST:
+        P.set_inspector(inspector)
     P.extract()
     if tiling:
         P.set_tiling(**tiling)

@@ -1,6 +1,9 @@
 // Band extractor: Appendix D, Algorithm 3 (ExtractBands) and Algorithm 4
 // (GrowSegments), with the FitRibbon step that Section 4.2 names but does not
-// define.  Host C++, threaded over rows where rows are independent.
+// define.  Host C++, threaded over rows where rows are independent; with the
+// device inspector, M[d] and FitRibbon over every row run on the GPU
+// (sable_inspect.cu) and GrowSegments walks the rows densely, with the same
+// results.
 //
 // Readings (identical to the library's documented behaviour):
 //  * M[d] counts residual entries on diagonal d = j - i, |d| <= d_max.
@@ -94,21 +97,63 @@ static inline int64_t ribbon_count(const Csr &R, int64_t r, int64_t olo, int64_t
   return R.count(r, r + olo, r + ohi);
 }
 
-std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p) {
+// GrowSegments (Algorithm 4) for offset d over consecutive rows that have a
+// ribbon (k > 0): list positions t in [0, len), rows[t] the row of position t
+// (ascending; rows = nullptr: position t is row t).  Shared by the listed-row form (host FitRibbon over the rows
+// holding an entry on d) and the dense form (device FitRibbon over every row).
+template <class K, class E>
+static void grow_segments(const Csr &R, int64_t d, const sable_extract_params &p, int64_t len, const int32_t *rows,
+                          K &&k_of, E &&ext_of, std::vector<BandSeg> &S) {
+  int64_t t = 0;
+  while (t < len) {
+    if (k_of(t) == 0) {
+      ++t;
+      continue;
+    }
+    const int64_t i0 = rows ? rows[t] : t;
+    int64_t L = ext_of(t).l, U = ext_of(t).u;
+    int64_t z = ribbon_count(R, i0, d - L, d + U);
+    int64_t j = i0 + 1, u = t + 1;
+    while (u < len && (rows ? rows[u] : u) == j && k_of(u) > 0) {
+      const Ext eu = ext_of(u);
+      const int64_t L2 = std::max<int64_t>(L, eu.l), U2 = std::max<int64_t>(U, eu.u);
+      int64_t z2;
+      if (L2 != L || U2 != U) {
+        z2 = 0;
+        for (int64_t r = i0; r <= j; ++r) z2 += ribbon_count(R, r, d - L2, d + U2);
+      } else {
+        z2 = z + ribbon_count(R, j, d - L, d + U);
+      }
+      if ((double)z2 / (double)((L2 + U2 + 1) * (j - i0 + 1)) < p.delta) break;
+      L = L2;
+      U = U2;
+      z = z2;
+      ++j;
+      ++u;
+    }
+    if (j - i0 >= p.l_seg) S.push_back({i0, j, d, L, U, z});
+    t = u;   // the next segment may start at row j (listed) or at the next listed row
+  }
+}
+
+std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p, DevResidual *dev) {
   const int64_t m = R.m, n = R.n;
   const int64_t d_max = p.d_max > 0 ? p.d_max : std::max(m, n);
   const int64_t count_min =
       p.count_min > 0 ? p.count_min : (int64_t)std::ceil(p.delta * (double)p.l_seg);
-  // M[d] over the offset range [-(m-1), n-1], and for every offset the rows
-  // holding a residual entry on it (ascending): FitRibbon(i, d) is (0, 0, 0)
-  // for every other row, so only these rows are visited.
+  // M[d] over the offset range [-(m-1), n-1]
   const int64_t span = m + n;
-  std::vector<int64_t> M(span > 0 ? span + 1 : 1, 0);
-  for (int64_t i = 0; i < m; ++i)
-    for (int64_t k = R.rp[i]; k < R.rp[i + 1]; ++k) {
-      const int64_t d = (int64_t)R.ci[k] - i;
-      if (d <= d_max && -d <= d_max) ++M[d + m];
-    }
+  std::vector<int64_t> M;
+  if (dev) {
+    if (sable_status st = dev_diag_counts(dev, d_max, M)) throw InspectError{st};
+  } else {
+    M.assign(span > 0 ? span + 1 : 1, 0);
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t k = R.rp[i]; k < R.rp[i + 1]; ++k) {
+        const int64_t d = (int64_t)R.ci[k] - i;
+        if (d <= d_max && -d <= d_max) ++M[d + m];
+      }
+  }
   std::vector<int64_t> D;
   for (int64_t t = 0; t < span; ++t)
     if (M[t] > 0 && M[t] >= count_min) D.push_back(t - m);
@@ -116,6 +161,54 @@ std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p) 
     if (M[a + m] != M[b + m]) return M[a + m] > M[b + m];
     return a < b;
   });
+
+  std::vector<uint8_t> used(m, 0);
+  std::vector<BandSeg> out;
+  auto accept = [&](std::vector<BandSeg> &S) {
+    if (S.empty()) return;
+    int64_t area = 0, zz = 0;
+    for (auto &sg : S) {
+      area += (sg.L + sg.U + 1) * (sg.i1 - sg.i0);
+      zz += sg.z;
+    }
+    if (area < p.a_min || (double)zz / (double)area < p.delta) return;
+    for (auto &sg : S) {
+      for (int64_t r = sg.i0; r < sg.i1; ++r) used[r] = 1;
+      out.push_back(sg);
+    }
+  };
+
+  if (dev) {
+    // FitRibbon on the device for every row and a chunk of candidates at a
+    // time (the results do not depend on the row mask, which is applied here)
+    const int w_max = (int)p.w_max;
+    std::vector<int32_t> zt(2 * (size_t)w_max + 2, 0);
+    for (int64_t w = 1; w < (int64_t)zt.size(); ++w) {
+      int64_t q = 0;
+      while (q <= w && (double)q / (double)w < p.delta) ++q;
+      zt[w] = (int32_t)q;
+    }
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(16ll << 20) / std::max<int64_t>(m, 1)));
+    std::vector<uint32_t> ext;
+    for (size_t c0 = 0; c0 < D.size(); c0 += chunk) {
+      const int nd = (int)std::min<int64_t>(chunk, (int64_t)D.size() - (int64_t)c0);
+      if (sable_status st = dev_fit_ribbons(dev, D.data() + c0, nd, w_max, zt, ext)) throw InspectError{st};
+      for (int c = 0; c < nd; ++c) {
+        const int64_t d = D[c0 + c];
+        const uint32_t *e = ext.data() + (size_t)c * (size_t)m;
+        std::vector<BandSeg> S;
+        grow_segments(
+            R, d, p, m, nullptr, [&](int64_t i) -> int64_t { return used[i] ? 0 : (int64_t)(e[i] >> 20); },
+            [&](int64_t i) { return Ext{(int32_t)(e[i] & 1023u), (int32_t)((e[i] >> 10) & 1023u), (int32_t)(e[i] >> 20)}; },
+            S);
+        accept(S);
+      }
+    }
+    return out;
+  }
+
+  // for every offset the rows holding a residual entry on it (ascending):
+  // FitRibbon(i, d) is (0, 0, 0) for every other row, so only these are visited
   std::vector<int64_t> start(span + 1, 0);
   for (int64_t t = 0; t < span; ++t) start[t + 1] = start[t] + M[t];
   std::vector<int32_t> drow(start[span]);
@@ -127,10 +220,7 @@ std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p) 
         if (d <= d_max && -d <= d_max) drow[pos[d + m]++] = (int32_t)i;
       }
   }
-
-  std::vector<uint8_t> used(m, 0);
   std::vector<Ext> ext;
-  std::vector<BandSeg> out;
   for (const int64_t d : D) {
     const int32_t *rows = drow.data() + start[d + m];
     const int64_t len = M[d + m];
@@ -141,48 +231,10 @@ std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p) 
     };
     if (len < 65536) fit(0, len);
     else parallel_rows(len, fit);
-    // GrowSegments (Algorithm 4) over the listed rows; an unlisted row has k = 0
     std::vector<BandSeg> S;
-    int64_t t = 0;
-    while (t < len) {
-      if (ext[t].k == 0) {
-        ++t;
-        continue;
-      }
-      const int64_t i0 = rows[t];
-      int64_t L = ext[t].l, U = ext[t].u;
-      int64_t z = ribbon_count(R, i0, d - L, d + U);
-      int64_t j = i0 + 1, u = t + 1;
-      while (u < len && rows[u] == j && ext[u].k > 0) {
-        const int64_t L2 = std::max<int64_t>(L, ext[u].l), U2 = std::max<int64_t>(U, ext[u].u);
-        int64_t z2;
-        if (L2 != L || U2 != U) {
-          z2 = 0;
-          for (int64_t r = i0; r <= j; ++r) z2 += ribbon_count(R, r, d - L2, d + U2);
-        } else {
-          z2 = z + ribbon_count(R, j, d - L, d + U);
-        }
-        if ((double)z2 / (double)((L2 + U2 + 1) * (j - i0 + 1)) < p.delta) break;
-        L = L2;
-        U = U2;
-        z = z2;
-        ++j;
-        ++u;
-      }
-      if (j - i0 >= p.l_seg) S.push_back({i0, j, d, L, U, z});
-      t = u;   // the next segment may start at row j (listed) or at the next listed row
-    }
-    if (S.empty()) continue;
-    int64_t area = 0, zz = 0;
-    for (auto &sg : S) {
-      area += (sg.L + sg.U + 1) * (sg.i1 - sg.i0);
-      zz += sg.z;
-    }
-    if (area < p.a_min || (double)zz / (double)area < p.delta) continue;
-    for (auto &sg : S) {
-      for (int64_t r = sg.i0; r < sg.i1; ++r) used[r] = 1;
-      out.push_back(sg);
-    }
+    grow_segments(
+        R, d, p, len, rows, [&](int64_t t) -> int64_t { return ext[t].k; }, [&](int64_t t) { return ext[t]; }, S);
+    accept(S);
   }
   return out;
 }

@@ -23,6 +23,8 @@
 //    row: the bounding box of its cells in that slab, grown by one cell in
 //    columns and, at the component's two ends, in rows.  Slabs touch but do
 //    not overlap, so the merge keeps them apart.
+//  With the device inspector the cell counts come from the GPU
+//  (sable_inspect.cu), with the same hot cells.
 //  The two scan shortcuts below (starting a window scan at the first
 //  non-empty histogram slot, stopping once the window is past the last one)
 //  reproduce the printed loop's results exactly, given delta > 0.
@@ -216,25 +218,34 @@ void trim(const Csr &R, const Csr &RT, int64_t &r0, int64_t &r1, int64_t &c0, in
   }
 }
 
-std::vector<Region> candidate_regions(const Csr &R, const sable_extract_params &p) {
+std::vector<Region> candidate_regions(const Csr &R, const sable_extract_params &p, DevResidual *dev) {
   const int64_t m = R.m, n = R.n, g = p.tile;
   const int64_t TI = (m + g - 1) / g, TJ = (n + g - 1) / g;
-  std::vector<int64_t> keys;
-  keys.reserve(R.nnz());
-  for (int64_t i = 0; i < m; ++i)
-    for (int64_t k = R.rp[i]; k < R.rp[i + 1]; ++k) keys.push_back((i / g) * TJ + R.ci[k] / g);
-  std::sort(keys.begin(), keys.end());
   std::vector<int64_t> hot;
-  for (size_t a = 0; a < keys.size();) {
-    size_t b = a;
-    while (b < keys.size() && keys[b] == keys[a]) ++b;
-    const int64_t I = keys[a] / TJ, J = keys[a] % TJ;
-    const int64_t area = std::min(g, m - I * g) * std::min(g, n - J * g);
-    if ((double)(b - a) >= p.delta * (double)area) hot.push_back(keys[a]);
-    a = b;
+  if (dev) {
+    // cell counts on the device; thr[a] = least count c with c >= delta * a (FP64)
+    std::vector<int32_t> thr(g * g + 1, 0);
+    for (int64_t a = 1; a <= g * g; ++a) {
+      int64_t c = 0;
+      while (c <= a && !((double)c >= p.delta * (double)a)) ++c;
+      thr[a] = (int32_t)c;
+    }
+    if (sable_status st = dev_hot_cells(dev, (int)g, thr, hot)) throw InspectError{st};
+  } else {
+    std::vector<int64_t> keys;
+    keys.reserve(R.nnz());
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t k = R.rp[i]; k < R.rp[i + 1]; ++k) keys.push_back((i / g) * TJ + R.ci[k] / g);
+    std::sort(keys.begin(), keys.end());
+    for (size_t a = 0; a < keys.size();) {
+      size_t b = a;
+      while (b < keys.size() && keys[b] == keys[a]) ++b;
+      const int64_t I = keys[a] / TJ, J = keys[a] % TJ;
+      const int64_t area = std::min(g, m - I * g) * std::min(g, n - J * g);
+      if ((double)(b - a) >= p.delta * (double)area) hot.push_back(keys[a]);
+      a = b;
+    }
   }
-  keys.clear();
-  keys.shrink_to_fit();
   std::vector<uint8_t> seen(hot.size(), 0);
   std::vector<std::array<int64_t, 4>> boxes;
   std::vector<size_t> stack, comp;
@@ -347,11 +358,12 @@ struct Partitioner {
 
 }  // namespace
 
-std::vector<BlockFound> partition_blocks(const Csr &R, const Csr &RT, const sable_extract_params &p) {
+std::vector<BlockFound> partition_blocks(const Csr &R, const Csr &RT, const sable_extract_params &p,
+                                         DevResidual *dev) {
   Partitioner P(R, RT, p);
   std::vector<Region> regions;
   if (p.tile <= 0) regions.push_back({0, R.m, 0, R.n});
-  else regions = candidate_regions(R, p);
+  else regions = candidate_regions(R, p, dev);
   for (const Region &g : regions) P.decompose(g.r0, g.r1, g.c0, g.c1);
   std::vector<BlockFound> out;
   int64_t covered = 0;

@@ -212,10 +212,32 @@ sable_status sable_plan_add_regions(sable_plan_t P, sable_extractor kind, const 
   return SABLE_OK;
 }
 
+sable_status sable_plan_set_inspector(sable_plan_t P, sable_inspector where) {
+  if (!P) return SABLE_ERR_INVALID;
+  if (P->sticky) return P->sticky;
+  if (P->extracted) return SABLE_ERR_ORDER;
+  if (where != SABLE_INSPECT_HOST && where != SABLE_INSPECT_DEVICE) return SABLE_ERR_INVALID;
+  P->inspector = (int)where;
+  return SABLE_OK;
+}
+
+namespace {
+// the device copy of one stage's residual, released on every way out
+struct DevStage {
+  sable::DevResidual *d = nullptr;
+  ~DevStage() { sable::dev_residual_close(d); }
+};
+}  // namespace
+
 sable_status sable_extract(sable_plan_t P) {
   if (!P) return SABLE_ERR_INVALID;
   if (P->sticky) return P->sticky;
   if (P->extracted) return SABLE_ERR_ORDER;
+  const bool on_device = P->inspector == SABLE_INSPECT_DEVICE;
+  if (on_device)
+    for (size_t st = 0; st < P->extractors.size(); ++st)
+      if (!P->stage_fixed[st] && P->extractors[st].first == SABLE_X_VBR && P->extractors[st].second.tile > 64)
+        return SABLE_ERR_UNSUPPORTED;
   try {
     alloc_point();
     const Csr &C = P->canon;
@@ -259,7 +281,10 @@ sable_status sable_extract(sable_plan_t P) {
       } else if (ex.first == SABLE_X_CSR) {
         for (int64_t q = 0; q < R.nnz(); ++q) P->owner[R.id[q]] = OWN_CSR;
       } else if (ex.first == SABLE_X_VDIA) {
-        for (const BandSeg &s : extract_bands(R, p)) {
+        DevStage ds;
+        if (on_device)
+          if (sable_status e = dev_residual_open(R, &ds.d)) return fail(P, e);
+        for (const BandSeg &s : extract_bands(R, p, ds.d)) {
           const int32_t sid = (int32_t)segs.size();
           segs.push_back({s.i0, s.i1 - s.i0, s.d - s.L, s.L + s.U + 1});
           sstage.push_back((int32_t)st);
@@ -274,7 +299,10 @@ sable_status sable_extract(sable_plan_t P) {
         }
       } else {
         Csr RT = residual(*P, true);
-        for (const BlockFound &b : partition_blocks(R, RT, p)) {
+        DevStage ds;
+        if (on_device && p.tile > 0)
+          if (sable_status e = dev_residual_open(R, &ds.d)) return fail(P, e);
+        for (const BlockFound &b : partition_blocks(R, RT, p, ds.d)) {
           const int32_t bid = (int32_t)blks.size();
           blks.push_back({b.r0, b.r1 - b.r0, b.c0, b.c1 - b.c0});
           bstage.push_back((int32_t)st);
@@ -372,6 +400,8 @@ sable_status sable_extract(sable_plan_t P) {
                    32 * (S.n_segments + S.n_blocks) + 4 * P->n + 4 * P->m;
   } catch (const std::bad_alloc &) {
     return fail(P, SABLE_ERR_OOM);
+  } catch (const InspectError &e) {
+    return fail(P, e.status);
   }
   P->extracted = true;
   return SABLE_OK;

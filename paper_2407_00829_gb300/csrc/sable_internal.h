@@ -160,6 +160,7 @@ struct sable_plan_s {
   int32_t *dev_err = nullptr;
   int device = -1;
   int sm_count = 0;
+  int inspector = 0;                   // sable_inspector of sable_extract
   sable_plan_stats stats{};
 };
 
@@ -171,13 +172,36 @@ sable_status fail(sable_plan_t p, sable_status s);
 // reaches this guarded allocation; both do nothing while injection is off.
 void alloc_point();
 bool alloc_fails();
+// sable_inspect.cu: the device inspector (the extractors' counting steps on the
+// GPU, integer arithmetic only).  A residual CSR copied to the current device,
+// with a stream of its own; every call is synchronous.
+struct DevResidual;
+sable_status dev_residual_open(const Csr &R, DevResidual **out);
+void dev_residual_close(DevResidual *D);
+// M[d + m] = residual entries on diagonal d, |d| <= d_max (size m + n + 1)
+sable_status dev_diag_counts(DevResidual *D, int64_t d_max, std::vector<int64_t> &M);
+// FitRibbon of every row for offsets ds[0, nd): ext[c m + i] = l | u << 10 | k << 20;
+// zt[w] = least q with q / w >= delta in FP64 (w + 1 if none), w in [0, 2 w_max + 1]
+sable_status dev_fit_ribbons(DevResidual *D, const int64_t *ds, int nd, int w_max, const std::vector<int32_t> &zt,
+                             std::vector<uint32_t> &ext);
+// keys I * TJ + J of the g x g cells whose count c has c >= delta * area in FP64,
+// i.e. c >= thr[area] (area in [1, g^2]), ascending
+sable_status dev_hot_cells(DevResidual *D, int g, const std::vector<int32_t> &thr, std::vector<int64_t> &hot);
+// a failed device inspector call, thrown through the extractors to sable_extract
+struct InspectError {
+  sable_status status;
+};
+
 // host_band.cpp: Algorithms 3 and 4; returns accepted segments (acceptance order)
-// as (row0, row_end, d, L, U).
+// as (row0, row_end, d, L, U).  With `dev`, M[d] and FitRibbon come from the
+// device inspector (same results).
 struct BandSeg { int64_t i0, i1, d, L, U, z; };
-std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p);
+std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p, DevResidual *dev = nullptr);
 // host_block.cpp: Algorithms 1 and 2; returns accepted blocks (acceptance order).
+// With `dev`, the candidate-region cell counts come from the device inspector.
 struct BlockFound { int64_t r0, r1, c0, c1, nnz; };
-std::vector<BlockFound> partition_blocks(const Csr &R, const Csr &RT, const sable_extract_params &p);
+std::vector<BlockFound> partition_blocks(const Csr &R, const Csr &RT, const sable_extract_params &p,
+                                         DevResidual *dev = nullptr);
 // threads used by the host extractors
 int host_threads();
 // sable_tc.cu: BF16 VBR blocks on the tensor cores

@@ -292,3 +292,42 @@ def test_passes_rejected_outside_range_and_for_other_kinds():
         with pytest.raises(sable.SableError):
             P.add_extractor(kind, passes=passes)
     P.close()
+
+
+def test_inspector_choice_rules():
+    A = synth.assemble(np.random.default_rng(2), 64, 64, bands=[(0, 0, 64)], n_scatter=50)
+    P = sable.Plan(A["m"], A["n"], A["row"], A["col"], A["val"])
+    with pytest.raises(sable.SableError) as e:
+        P.set_inspector(2)
+    assert e.value.status == 1
+    # a block stage whose pre-pass tiles exceed what the device counts: refused, not sticky
+    P.add_extractor(sable.VBR, tile=65).add_extractor(sable.CSR)
+    P.set_inspector(sable.INSPECT_DEVICE)
+    with pytest.raises(sable.SableError) as e:
+        P.extract()
+    assert e.value.status == 8
+    assert P.status() == 0
+    P.set_inspector(sable.INSPECT_HOST).extract()
+    with pytest.raises(sable.SableError) as e:
+        P.set_inspector(sable.INSPECT_DEVICE)                 # after extract
+    assert e.value.status == 5
+    P.close()
+
+
+def test_device_inspector_without_a_gpu_reports_cuda_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the device inspector's parity tests cover it")
+    A = synth.assemble(np.random.default_rng(3), 128, 128, bands=[(0, 0, 128)], n_scatter=50)
+    P = sable.Plan(A["m"], A["n"], A["row"], A["col"], A["val"])
+    P.add_extractor(sable.VDIA).add_extractor(sable.CSR).set_inspector(sable.INSPECT_DEVICE)
+    with pytest.raises(sable.SableError) as e:
+        P.extract()
+    assert e.value.status == 3
+    assert P.status() == 3
+    P.close()
+    # a plan whose stages need no device counting makes no CUDA call
+    P = sable.Plan(A["m"], A["n"], A["row"], A["col"], A["val"])
+    P.add_extractor(sable.VBR, tile=0).add_extractor(sable.CSR).set_inspector(sable.INSPECT_DEVICE).extract()
+    assert P.info()["nnz"] == A["row"].size
+    P.close()

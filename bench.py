@@ -562,6 +562,13 @@ def run_planner(args):
     for i in range(max(1, min(args.steps, 3))):
         A = synth.planner_set_matrix(200_000 + i)
         best, t, t_exh = pl.exhaustive(A, op=0)
+        # the exhaustive planner's candidate extractions alone, host and device inspector
+        ext_s = {}
+        for label, where in (("host", 0), ("device", 1)):
+            t0 = time.perf_counter()
+            for P in pl.build_plans(A, upload=False, inspector=where):
+                P.close()
+            ext_s[label] = round(time.perf_counter() - t0, 3)
         t0 = time.perf_counter()
         name = lp.plan(A, N=0)
         spec = dict(pl.CANDIDATES)[name]
@@ -574,7 +581,8 @@ def run_planner(args):
         live.append({"m": A["m"], "nnz": int(A["row"].size), "learned": name, "exhaustive": pl.NAMES[best],
                      "spmv_ms_learned": t[k], "spmv_ms_best": t[best],
                      "spmv_ms_default": t[pl.NAMES.index(pl.DEFAULT)],
-                     "planning_s_learned": round(t_learned, 3), "planning_s_exhaustive": round(t_exh, 3)})
+                     "planning_s_learned": round(t_learned, 3), "planning_s_exhaustive": round(t_exh, 3),
+                     "candidate_extraction_s": ext_s})
     value = float(np.mean([res["learned"][op]["mean_loss"] for op, _ in pl.OPS]))
     line = {"metric": "learned planner: mean plan-quality loss t_chosen / t_exhaustive - 1 (held-out)",
             "value": value, "unit": "fraction", "n_gpus": 1, "steps": len(live), "warmup": 0,

@@ -70,10 +70,12 @@ def _new_plan(A) -> Plan:
     return Plan(A["m"], A["n"], A["row"], A["col"], A["val"])
 
 
-def _extract(A, spec) -> Plan:
+def _extract(A, spec, inspector: int = 0) -> Plan:
     P = _new_plan(A)
     for kind, kw in spec:
         P.add_extractor(kind, **(kw or {}))
+    if inspector:
+        P.set_inspector(inspector)
     return P.extract()
 
 
@@ -160,13 +162,14 @@ def time_candidates(plans, A, x, y, B, C, top=3):
     return t
 
 
-def build_plans(A, tables=None, workers=9, upload=True):
+def build_plans(A, tables=None, workers=9, upload=True, inspector: int = 0):
     """All candidate plans of A (uploaded unless upload=False): from region
-    tables when given."""
+    tables when given; searched with the host inspector, or with the device
+    inspector (INSPECT_DEVICE: the same plans)."""
     def one(c):
         name, spec = CANDIDATES[c]
         if tables is None:
-            return _extract(A, spec)
+            return _extract(A, spec, inspector)
         return _new_plan(A).add_stages(tables[name]).extract()
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         plans = list(ex.map(one, range(len(CANDIDATES))))
@@ -186,10 +189,10 @@ def _operands(A, seed):
     return x, y, B, C
 
 
-def exhaustive(A, op=0, tables=None):
+def exhaustive(A, op=0, tables=None, inspector: int = 0):
     """The exhaustive planner: (best candidate index, ms per candidate, seconds)."""
     t0 = time.perf_counter()
-    plans = build_plans(A, tables)
+    plans = build_plans(A, tables, inspector=inspector)
     x, y, B, C = _operands(A, 0)
     t = [time_plan(P, A, x, y, B, C)[op] for P in plans]
     for P in plans:

@@ -280,8 +280,8 @@ sable_status sable_plan_set_spmm_depth(sable_plan_t plan, int32_t depth);
  * x, out = y), 4 = plain CSR SpMV (sable_csr_spmv), 1 = SpMM FP32, 2 = SpMM
  * with BF16 blocks, 3 = SpMM with SABLE_FP32_SPLIT blocks (in = B, n x N, out =
  * C, m x N, row-major with leading dimension N); in / out are device buffers
- * the timed launches read and overwrite.  Candidates: SpMV rows {128, 256,
- * 512, 1024} x bytes {16K, 48K, 160K}, and 1024 rows with the bytes that cut
+ * the timed launches read and overwrite.  Candidates: SpMV rows {32, 64, 128,
+ * 256, 512, 1024} x bytes {4K, 16K, 48K, 160K}, and 1024 rows with the bytes that cut
  * the plan into 1, 2 or 3 full waves of the CTAs the GPU holds at once; SpMM
  * (column panel, rows in flight) in {128, 64, 32} x {4, 8}; the other op's
  * tiling is kept.  Each candidate is

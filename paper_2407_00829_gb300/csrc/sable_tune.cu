@@ -122,8 +122,9 @@ sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *
   }
   if (!cached) {
     if (spmv) {
-      for (int32_t rows : {128, 256, 512, 1024})
-        for (int64_t bytes : {16 << 10, 48 << 10, 160 << 10})
+      // short tiles (32, 64 rows) give small matrices enough CTAs to fill the GPU
+      for (int32_t rows : {32, 64, 128, 256, 512, 1024})
+        for (int64_t bytes : {4 << 10, 16 << 10, 48 << 10, 160 << 10})
           cand.push_back({rows, bytes, cur.spmm_cols, cur.spmm_depth});
       // tiles sized for exactly 1, 2 or 3 full waves of resident CTAs
       int dev = 0, sms = 0;

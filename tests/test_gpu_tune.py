@@ -11,7 +11,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-SPMV_ROWS, SPMV_BYTES = {128, 256, 512, 1024}, {16 << 10, 48 << 10, 160 << 10}
+SPMV_ROWS, SPMV_BYTES = {32, 64, 128, 256, 512, 1024}, {4 << 10, 16 << 10, 48 << 10, 160 << 10}
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -53,6 +53,10 @@ def _args():
                     help="batch workload: keep the default tiling (a short command to profile)")
     ap.add_argument("--spmm-only", action="store_true",
                     help="only the SpMM workload, default tiling, no tuning (a short command to profile)")
+    ap.add_argument("--spmm-tiling", default=None, metavar="COLS,DEPTH",
+                    help="--spmm-only: row-kernel column panel and B rows in flight instead of the default")
+    ap.add_argument("--spmm-ops", default="fp32,fp32_split,bf16_blocks,plain_csr",
+                    help="--spmm-only: comma-separated subset of fp32,fp32_split,bf16_blocks,plain_csr")
     return ap.parse_args()
 
 
@@ -514,16 +518,24 @@ def run_spmm_only(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     A = synth.blocks_scatter_200k()
-    P = sable.plan_from(A, [(sable.VBR, dict(a_min=256)), (sable.CSR, None)])
+    P = sable.plan_from(A, [(sable.VBR, dict(a_min=256)), (sable.CSR, None)], upload=False)
+    tiling = "default tiling"
+    if args.spmm_tiling:
+        cols, depth = (int(v) for v in args.spmm_tiling.split(","))
+        P.set_tiling(spmm_cols=cols, spmm_depth=depth)
+        tiling = f"column panel {cols}, {depth} B rows in flight"
+    P.upload(stream)
     N = 128
     B = torch.from_numpy(synth.dense_operand(13, A["n"], N)).to(dev)
     C = torch.empty(A["m"], N, device=dev)
-    out = {"workload": "spmm-vbr+csr-200k, N=128, default tiling", "ms": {}}
+    out = {"workload": f"spmm-vbr+csr-200k, N=128, {tiling}", "ms": {}}
     k = max(1, min(args.steps, 20))
-    for name, fn in (("fp32", lambda: P.spmm(B, C, sable.FP32, stream)),
-                     ("fp32_split", lambda: P.spmm(B, C, sable.FP32_SPLIT, stream)),
-                     ("bf16_blocks", lambda: P.spmm(B, C, sable.BF16_BLOCKS, stream)),
-                     ("plain_csr", lambda: P.csr_spmm(B, C, stream))):
+    ops = {"fp32": lambda: P.spmm(B, C, sable.FP32, stream),
+           "fp32_split": lambda: P.spmm(B, C, sable.FP32_SPLIT, stream),
+           "bf16_blocks": lambda: P.spmm(B, C, sable.BF16_BLOCKS, stream),
+           "plain_csr": lambda: P.csr_spmm(B, C, stream)}
+    for name in args.spmm_ops.split(","):
+        fn = ops[name]
         for _ in range(3):
             fn()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -232,19 +232,37 @@ std::vector<Region> candidate_regions(const Csr &R, const sable_extract_params &
     }
     if (sable_status st = dev_hot_cells(dev, (int)g, thr, hot)) throw InspectError{st};
   } else {
-    std::vector<int64_t> keys;
-    keys.reserve(R.nnz());
-    for (int64_t i = 0; i < m; ++i)
-      for (int64_t k = R.rp[i]; k < R.rp[i + 1]; ++k) keys.push_back((i / g) * TJ + R.ci[k] / g);
-    std::sort(keys.begin(), keys.end());
-    for (size_t a = 0; a < keys.size();) {
-      size_t b = a;
-      while (b < keys.size() && keys[b] == keys[a]) ++b;
-      const int64_t I = keys[a] / TJ, J = keys[a] % TJ;
-      const int64_t area = std::min(g, m - I * g) * std::min(g, n - J * g);
-      if ((double)(b - a) >= p.delta * (double)area) hot.push_back(keys[a]);
-      a = b;
+    // per tile row: the cells of its entries, sorted, counted in runs; tile
+    // rows in parallel, concatenated in order (keys ascending)
+    const int T = R.nnz() >= (1 << 20) ? host_threads() : 1;
+    std::vector<std::vector<int64_t>> part(T);
+    const int64_t per = (TI + T - 1) / T;
+    auto work = [&](int t) {
+      std::vector<int32_t> cells;
+      const int64_t I1 = std::min(TI, (t + 1) * per);
+      for (int64_t I = t * per; I < I1; ++I) {
+        const int64_t r0 = I * g, r1 = std::min(m, r0 + g);
+        cells.clear();
+        for (int64_t k = R.rp[r0]; k < R.rp[r1]; ++k) cells.push_back((int32_t)(R.ci[k] / g));
+        std::sort(cells.begin(), cells.end());
+        for (size_t a = 0; a < cells.size();) {
+          size_t b = a;
+          while (b < cells.size() && cells[b] == cells[a]) ++b;
+          const int64_t J = cells[a];
+          const int64_t area = (r1 - r0) * std::min(g, n - J * g);
+          if ((double)(b - a) >= p.delta * (double)area) part[t].push_back(I * TJ + J);
+          a = b;
+        }
+      }
+    };
+    if (T == 1) {
+      work(0);
+    } else {
+      std::vector<std::thread> th;
+      for (int t = 0; t < T; ++t) th.emplace_back(work, t);
+      for (auto &x : th) x.join();
     }
+    for (auto &v : part) hot.insert(hot.end(), v.begin(), v.end());
   }
   std::vector<uint8_t> seen(hot.size(), 0);
   std::vector<std::array<int64_t, 4>> boxes;

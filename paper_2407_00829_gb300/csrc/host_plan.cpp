@@ -3,6 +3,7 @@
 // "Initialize" / "Extract"), the completeness check (Section 3, "Dispatch"),
 // and host exports.  No CUDA call is made here.
 #include <algorithm>
+#include <thread>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -39,27 +40,73 @@ sable_status fail(sable_plan_t p, sable_status s) {
 }
 
 // Residual (owner < 0) of the canonical matrix as CSR, or its transpose.
+// Rows (or columns) keep their inner indices ascending.  Threads over row
+// ranges on large matrices: each range counts its entries per output line,
+// the counts are turned into per-range offsets line by line, and each range
+// fills its own slots (ranges in row order, so every line stays sorted).
 static Csr residual(const sable_plan_s &P, bool transpose) {
   Csr R;
+  const Csr &C = P.canon;
   R.m = transpose ? P.n : P.m;
   R.n = transpose ? P.m : P.n;
   R.rp.assign(R.m + 1, 0);
-  const Csr &C = P.canon;
-  for (int64_t i = 0; i < C.m; ++i)
-    for (int64_t k = C.rp[i]; k < C.rp[i + 1]; ++k)
-      if (P.owner[k] < 0) ++R.rp[(transpose ? C.ci[k] : i) + 1];
-  for (int64_t i = 0; i < R.m; ++i) R.rp[i + 1] += R.rp[i];
+  const int T = std::max(1, std::min(C.nnz() >= (1 << 20) ? host_threads() : 1, (int)std::max<int64_t>(C.m, 1)));
+  const int64_t chunk = (C.m + T - 1) / T;
+  auto run = [&](auto &&f) {
+    if (T == 1) {
+      f(0);
+      return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t) th.emplace_back(f, t);
+    for (auto &x : th) x.join();
+  };
+  // cnt[t][o]: entries of range t on output line o, then that range's first slot on line o
+  // (int32: a plan holds fewer than 2^31 entries)
+  std::vector<std::vector<int32_t>> cnt(T, std::vector<int32_t>(transpose ? R.m : 0, 0));
+  std::vector<int64_t> rowcnt(transpose ? 0 : C.m, 0);
+  run([&](int t) {
+    const int64_t a = t * chunk, b = std::min(C.m, a + chunk);
+    for (int64_t i = a; i < b; ++i)
+      for (int64_t k = C.rp[i]; k < C.rp[i + 1]; ++k)
+        if (P.owner[k] < 0) {
+          if (transpose) ++cnt[t][C.ci[k]];
+          else ++rowcnt[i];
+        }
+  });
+  if (transpose) {
+    for (int64_t o = 0; o < R.m; ++o) {
+      int64_t at = R.rp[o];
+      for (int t = 0; t < T; ++t) {
+        const int64_t c = cnt[t][o];
+        cnt[t][o] = (int32_t)at;
+        at += c;
+      }
+      R.rp[o + 1] = at;
+    }
+  } else {
+    for (int64_t i = 0; i < C.m; ++i) R.rp[i + 1] = R.rp[i] + rowcnt[i];
+  }
   R.ci.resize(R.rp[R.m]);
   R.id.resize(R.rp[R.m]);
-  std::vector<int64_t> pos(R.rp.begin(), R.rp.end() - 1);
-  for (int64_t i = 0; i < C.m; ++i)   // row-major sweep keeps inner indices sorted
-    for (int64_t k = C.rp[i]; k < C.rp[i + 1]; ++k) {
-      if (P.owner[k] >= 0) continue;
-      const int64_t o = transpose ? C.ci[k] : i;
-      const int64_t q = pos[o]++;
-      R.ci[q] = transpose ? (int32_t)i : C.ci[k];
-      R.id[q] = k;
+  run([&](int t) {
+    const int64_t a = t * chunk, b = std::min(C.m, a + chunk);
+    for (int64_t i = a; i < b; ++i) {
+      int64_t q = transpose ? 0 : R.rp[i];
+      for (int64_t k = C.rp[i]; k < C.rp[i + 1]; ++k) {
+        if (P.owner[k] >= 0) continue;
+        if (transpose) {
+          const int64_t s = cnt[t][C.ci[k]]++;
+          R.ci[s] = (int32_t)i;
+          R.id[s] = k;
+        } else {
+          R.ci[q] = C.ci[k];
+          R.id[q] = k;
+          ++q;
+        }
+      }
     }
+  });
   return R;
 }
 
@@ -124,25 +171,53 @@ sable_status sable_plan_create(int64_t m, int64_t n, int64_t nnz, const int32_t 
     C.m = m;
     C.n = n;
     C.rp.assign(m + 1, 0);
-    C.ci.reserve(nnz);
-    P->cval.reserve(nnz);
     P->canon_of.assign(nnz, 0);
-    for (int64_t i = 0; i < m; ++i) {
-      int64_t *b = order.data() + cnt[i], *e = order.data() + cnt[i + 1];
-      std::stable_sort(b, e, [&](int64_t a, int64_t z) { return col[a] < col[z]; });
-      for (int64_t *q = b; q < e;) {
-        const int32_t c = col[*q];
-        const int32_t id = (int32_t)C.ci.size();
-        double s = 0.0;
-        for (; q < e && col[*q] == c; ++q) {   // input order
-          s += (double)val[*q];
-          P->canon_of[*q] = id;
-        }
-        C.ci.push_back(c);
-        P->cval.push_back((float)s);
+    // rows are independent: sort each row's bucket by column (stable: equal
+    // columns keep input order) and count its distinct columns, then fill;
+    // threads over row ranges on large matrices, the same result either way
+    const int T = nnz >= (1 << 20) ? host_threads() : 1;
+    auto over_rows = [&](auto &&f) {
+      if (T <= 1) {
+        f(0, m);
+        return;
       }
-      C.rp[i + 1] = (int64_t)C.ci.size();
-    }
+      std::vector<std::thread> th;
+      const int64_t chunk = (m + T - 1) / T;
+      for (int t = 0; t < T; ++t) {
+        const int64_t a = t * chunk, b = std::min(m, a + chunk);
+        if (a >= b) break;
+        th.emplace_back([&f, a, b] { f(a, b); });
+      }
+      for (auto &x : th) x.join();
+    };
+    over_rows([&](int64_t a, int64_t b) {
+      for (int64_t i = a; i < b; ++i) {
+        int64_t *q = order.data() + cnt[i], *e = order.data() + cnt[i + 1];
+        std::stable_sort(q, e, [&](int64_t u, int64_t z) { return col[u] < col[z]; });
+        int64_t distinct = 0;
+        for (int64_t *r = q; r < e; ++r) distinct += (r == q || col[*r] != col[*(r - 1)]);
+        C.rp[i + 1] = distinct;
+      }
+    });
+    for (int64_t i = 0; i < m; ++i) C.rp[i + 1] += C.rp[i];
+    C.ci.resize(C.rp[m]);
+    P->cval.resize(C.rp[m]);
+    over_rows([&](int64_t a, int64_t b) {
+      for (int64_t i = a; i < b; ++i) {
+        int64_t id = C.rp[i];
+        const int64_t *e = order.data() + cnt[i + 1];
+        for (const int64_t *q = order.data() + cnt[i]; q < e; ++id) {
+          const int32_t c = col[*q];
+          double sum = 0.0;
+          for (; q < e && col[*q] == c; ++q) {   // input order
+            sum += (double)val[*q];
+            P->canon_of[*q] = (int32_t)id;
+          }
+          C.ci[id] = c;
+          P->cval[id] = (float)sum;
+        }
+      }
+    });
     C.id.clear();
     P->owner.assign(C.ci.size(), OWN_NONE);
   } catch (const std::bad_alloc &) {

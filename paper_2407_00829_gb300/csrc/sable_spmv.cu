@@ -31,6 +31,23 @@ namespace sable {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
 
+// Streamed operands (VDIA values, CSR values and columns) are read once: they
+// bypass L1 allocation, which leaves L1 to the x gathers that hit it.
+__device__ __forceinline__ float4 ld_stream_f4(const float *p) {
+  float4 r;
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+      : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+      : "l"(p));
+  return r;
+}
+__device__ __forceinline__ int4 ld_stream_i4(const int *p) {
+  int4 r;
+  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p));
+  return r;
+}
+
 template <bool PLAIN>
 __device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T, const DevItem &I,
                                           const float *__restrict__ x, float *__restrict__ y, float *ys,
@@ -62,7 +79,7 @@ __device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T,
         const int c0 = my + s.off_lo;
 #pragma unroll 1
         for (int k = jj; k < s.ndiag; k += S) {
-          const float4 v = __ldg(reinterpret_cast<const float4 *>(vp + (size_t)k * s.ld));
+          const float4 v = ld_stream_f4(vp + (size_t)k * s.ld);
           const int c = c0 + k;
           const float x0 = (g0 && (unsigned)c < n) ? __ldg(x + c) : 0.f;
           const float x1 = (g1 && (unsigned)(c + 1) < n) ? __ldg(x + c + 1) : 0.f;
@@ -110,8 +127,8 @@ __device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T,
       int row = -1 - lane;
       float run = 0.f;
       if (p0 < pe && p0 + 4 > pb) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(A.cv + p0));
-        const int4 c = __ldg(reinterpret_cast<const int4 *>(A.ci + p0));
+        const float4 v = ld_stream_f4(A.cv + p0);
+        const int4 c = ld_stream_i4(A.ci + p0);
         const int pf = max(p0, pb);
         int lo = 0, hi = R;                 // rps[lo] <= pf < rps[hi]
         while (hi - lo > 1) {

@@ -286,8 +286,11 @@ sable_status sable_plan_set_spmm_depth(sable_plan_t plan, int32_t depth);
  * (column panel, rows in flight) in {128, 64, 32} x {4, 8}; the other op's
  * tiling is kept.  Each candidate is
  * uploaded (sable_plan_upload, which reallocates the plan's device tables and
- * waits for the device), run twice, then timed as the best of two rounds of
- * `reps` back-to-back launches.  The winner is remembered per shape class
+ * waits for the device), then timed as the best of two rounds of `reps`
+ * launches: for the SpMV ops the `reps` launches are captured in one CUDA
+ * graph on a stream of the library's own and the graph is replayed on
+ * `stream` (a small plan's launch is shorter than the host's work per call);
+ * for SpMM, after two warm-up runs, `reps` back-to-back launches.  The winner is remembered per shape class
  * (op, floor log2 of N, m and nnz, and the quarters of the entries in VDIA
  * and in VBR) for the life of the process; with use_cache != 0 a known class
  * is applied and timed without a search.  chosen / chosen_ms (host, may be

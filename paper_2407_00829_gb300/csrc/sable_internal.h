@@ -161,6 +161,8 @@ struct sable_plan_s {
   int device = -1;
   int sm_count = 0;
   int inspector = 0;                   // sable_inspector of sable_extract
+  int spmv_occ[2] = {0, 0};            // resident SpMV CTAs per SM (hybrid, plain) at ...
+  size_t spmv_occ_smem[2] = {0, 0};    // ... this dynamic shared memory per CTA
   sable_plan_stats stats{};
 };
 

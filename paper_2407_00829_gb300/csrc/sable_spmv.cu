@@ -217,9 +217,17 @@ sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const f
   if (D.spmv.rows_max > 4 * kThreads) return fail(P, SABLE_ERR_INVALID);
   const size_t smem = (size_t)D.spmv.rows_max * 4 + ((size_t)D.spmv.rows_max + 1) * 4;
   auto k = plain ? spmv_hybrid_kernel<true> : spmv_hybrid_kernel<false>;
-  int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
+  // resident CTAs per SM for this shared-memory size, queried once per plan
+  // and size (the query costs host time on every call of a small matrix)
+  const int which = plain ? 1 : 0;
+  int per_sm = P->spmv_occ[which];
+  if (per_sm < 1 || P->spmv_occ_smem[which] != smem) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    (void)cudaGetLastError();
+    P->spmv_occ[which] = per_sm;
+    P->spmv_occ_smem[which] = smem;
+  }
   const int grid = std::max(1, std::min(D.spmv.n, per_sm * std::max(P->sm_count, 1)));
   k<<<grid, kThreads, smem, st>>>(D, x, y);
   if (cudaGetLastError() != cudaSuccess) {

@@ -164,3 +164,41 @@ def test_device_inspected_plan_computes_like_the_host_one():
         assert oracle.normwise_err(y.cpu().numpy(), ref) <= 1e-5
     H.close()
     D.close()
+
+
+def test_device_inspector_allocation_failures_return_oom_and_free_memory():
+    """Allocation-failure injection at each guarded allocation of a device
+    extraction (plan tables on the host, the residual's device copy, the
+    histogram, ribbon and cell-key buffers): the extraction returns
+    SABLE_ERR_OOM and keeps it as the plan's status, or succeeds with the host
+    inspector's plan once the countdown passes every allocation; device memory
+    is back where it started."""
+    import torch
+    L = sable.lib()
+    A = synth.blocks_bands_scatter_4096()
+    spec = [(sable.VDIA, None), (sable.VBR, None), (sable.CSR, None)]
+    H = sable.plan_from(A, spec, upload=False)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    outcomes = []
+    try:
+        for k in range(12):
+            P = sable.Plan(A["m"], A["n"], A["row"], A["col"], A["val"])
+            for kind, kw in spec:
+                P.add_extractor(kind, **(kw or {}))
+            P.set_inspector(sable.INSPECT_DEVICE)
+            L.sable_debug_fail_allocations(k)
+            st = L.sable_extract(P.handle)
+            L.sable_debug_fail_allocations(-1)
+            outcomes.append(st)
+            if st == 0:
+                _same(H, P)
+            else:
+                assert st == 2 and L.sable_plan_status(P.handle) == 2
+            P.close()
+    finally:
+        L.sable_debug_fail_allocations(-1)
+    assert 2 in outcomes and outcomes[-1] == 0          # some allocation failed; late enough, none does
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (8 << 20)
+    H.close()

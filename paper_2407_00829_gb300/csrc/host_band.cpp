@@ -1,9 +1,8 @@
 // Band extractor: Appendix D, Algorithm 3 (ExtractBands) and Algorithm 4
 // (GrowSegments), with the FitRibbon step that Section 4.2 names but does not
 // define.  Host C++, threaded over rows where rows are independent; with the
-// device inspector, M[d] and FitRibbon over every row run on the GPU
-// (sable_inspect.cu) and GrowSegments walks the rows densely, with the same
-// results.
+// device inspector, M[d] and FitRibbon of every entry on a candidate diagonal
+// run on the GPU (sable_inspect.cu), with the same results.
 //
 // Readings (identical to the library's documented behaviour):
 //  * M[d] counts residual entries on diagonal d = j - i, |d| <= d_max.
@@ -97,10 +96,10 @@ static inline int64_t ribbon_count(const Csr &R, int64_t r, int64_t olo, int64_t
   return R.count(r, r + olo, r + ohi);
 }
 
-// GrowSegments (Algorithm 4) for offset d over consecutive rows that have a
-// ribbon (k > 0): list positions t in [0, len), rows[t] the row of position t
-// (ascending; rows = nullptr: position t is row t).  Shared by the listed-row form (host FitRibbon over the rows
-// holding an entry on d) and the dense form (device FitRibbon over every row).
+// GrowSegments (Algorithm 4) for offset d over the rows holding an entry on d:
+// list positions t in [0, len), rows[t] ascending; k_of(t) = 0 where FitRibbon
+// gave no ribbon (or the row is masked), ext_of(t) its (l, u, k).  Shared by
+// the host FitRibbon and the device inspector's.
 template <class K, class E>
 static void grow_segments(const Csr &R, int64_t d, const sable_extract_params &p, int64_t len, const int32_t *rows,
                           K &&k_of, E &&ext_of, std::vector<BandSeg> &S) {
@@ -110,11 +109,11 @@ static void grow_segments(const Csr &R, int64_t d, const sable_extract_params &p
       ++t;
       continue;
     }
-    const int64_t i0 = rows ? rows[t] : t;
+    const int64_t i0 = rows[t];
     int64_t L = ext_of(t).l, U = ext_of(t).u;
     int64_t z = ribbon_count(R, i0, d - L, d + U);
     int64_t j = i0 + 1, u = t + 1;
-    while (u < len && (rows ? rows[u] : u) == j && k_of(u) > 0) {
+    while (u < len && rows[u] == j && k_of(u) > 0) {
       const Ext eu = ext_of(u);
       const int64_t L2 = std::max<int64_t>(L, eu.l), U2 = std::max<int64_t>(U, eu.u);
       int64_t z2;
@@ -178,9 +177,29 @@ std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p, 
     }
   };
 
+  // for every offset the rows holding a residual entry on it (ascending), and
+  // where that entry sits in the residual: FitRibbon(i, d) is (0, 0, 0) for
+  // every other row, so only these are visited
+  std::vector<int64_t> start(span + 1, 0);
+  for (int64_t t = 0; t < span; ++t) start[t + 1] = start[t] + M[t];
+  std::vector<int32_t> drow(start[span]);
+  std::vector<int64_t> dpos(dev ? start[span] : 0);
+  {
+    std::vector<int64_t> pos(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t k = R.rp[i]; k < R.rp[i + 1]; ++k) {
+        const int64_t d = (int64_t)R.ci[k] - i;
+        if (d <= d_max && -d <= d_max) {
+          const int64_t q = pos[d + m]++;
+          drow[q] = (int32_t)i;
+          if (dev) dpos[q] = k;
+        }
+      }
+  }
+  // device inspector: FitRibbon of every entry on a candidate diagonal in one
+  // launch (the results do not depend on the row mask, applied below)
+  std::vector<uint32_t> ext_e;
   if (dev) {
-    // FitRibbon on the device for every row and a chunk of candidates at a
-    // time (the results do not depend on the row mask, which is applied here)
     const int w_max = (int)p.w_max;
     std::vector<int32_t> zt(2 * (size_t)w_max + 2, 0);
     for (int64_t w = 1; w < (int64_t)zt.size(); ++w) {
@@ -188,52 +207,35 @@ std::vector<BandSeg> extract_bands(const Csr &R, const sable_extract_params &p, 
       while (q <= w && (double)q / (double)w < p.delta) ++q;
       zt[w] = (int32_t)q;
     }
-    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(16ll << 20) / std::max<int64_t>(m, 1)));
-    std::vector<uint32_t> ext;
-    for (size_t c0 = 0; c0 < D.size(); c0 += chunk) {
-      const int nd = (int)std::min<int64_t>(chunk, (int64_t)D.size() - (int64_t)c0);
-      if (sable_status st = dev_fit_ribbons(dev, D.data() + c0, nd, w_max, zt, ext)) throw InspectError{st};
-      for (int c = 0; c < nd; ++c) {
-        const int64_t d = D[c0 + c];
-        const uint32_t *e = ext.data() + (size_t)c * (size_t)m;
-        std::vector<BandSeg> S;
-        grow_segments(
-            R, d, p, m, nullptr, [&](int64_t i) -> int64_t { return used[i] ? 0 : (int64_t)(e[i] >> 20); },
-            [&](int64_t i) { return Ext{(int32_t)(e[i] & 1023u), (int32_t)((e[i] >> 10) & 1023u), (int32_t)(e[i] >> 20)}; },
-            S);
-        accept(S);
-      }
-    }
-    return out;
-  }
-
-  // for every offset the rows holding a residual entry on it (ascending):
-  // FitRibbon(i, d) is (0, 0, 0) for every other row, so only these are visited
-  std::vector<int64_t> start(span + 1, 0);
-  for (int64_t t = 0; t < span; ++t) start[t + 1] = start[t] + M[t];
-  std::vector<int32_t> drow(start[span]);
-  {
-    std::vector<int64_t> pos(start.begin(), start.end() - 1);
-    for (int64_t i = 0; i < m; ++i)
-      for (int64_t k = R.rp[i]; k < R.rp[i + 1]; ++k) {
-        const int64_t d = (int64_t)R.ci[k] - i;
-        if (d <= d_max && -d <= d_max) drow[pos[d + m]++] = (int32_t)i;
-      }
+    std::vector<unsigned char> cand(span + 1, 0);
+    for (const int64_t d : D) cand[d + m] = 1;
+    if (sable_status st = dev_fit_ribbons(dev, d_max, cand, w_max, zt, ext_e)) throw InspectError{st};
   }
   std::vector<Ext> ext;
   for (const int64_t d : D) {
     const int32_t *rows = drow.data() + start[d + m];
     const int64_t len = M[d + m];
-    ext.resize(len);
-    auto fit = [&](int64_t a, int64_t b) {
-      for (int64_t t = a; t < b; ++t)
-        ext[t] = used[rows[t]] ? Ext{0, 0, 0} : fit_ribbon(R, rows[t], d, p.delta, p.w_max);
-    };
-    if (len < 65536) fit(0, len);
-    else parallel_rows(len, fit);
     std::vector<BandSeg> S;
-    grow_segments(
-        R, d, p, len, rows, [&](int64_t t) -> int64_t { return ext[t].k; }, [&](int64_t t) { return ext[t]; }, S);
+    if (dev) {
+      const int64_t *at = dpos.data() + start[d + m];
+      grow_segments(
+          R, d, p, len, rows, [&](int64_t t) -> int64_t { return used[rows[t]] ? 0 : (int64_t)(ext_e[at[t]] >> 20); },
+          [&](int64_t t) {
+            const uint32_t e = ext_e[at[t]];
+            return Ext{(int32_t)(e & 1023u), (int32_t)((e >> 10) & 1023u), (int32_t)(e >> 20)};
+          },
+          S);
+    } else {
+      ext.resize(len);
+      auto fit = [&](int64_t a, int64_t b) {
+        for (int64_t t = a; t < b; ++t)
+          ext[t] = used[rows[t]] ? Ext{0, 0, 0} : fit_ribbon(R, rows[t], d, p.delta, p.w_max);
+      };
+      if (len < 65536) fit(0, len);
+      else parallel_rows(len, fit);
+      grow_segments(
+          R, d, p, len, rows, [&](int64_t t) -> int64_t { return ext[t].k; }, [&](int64_t t) { return ext[t]; }, S);
+    }
     accept(S);
   }
   return out;

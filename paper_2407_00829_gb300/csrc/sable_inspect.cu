@@ -3,8 +3,9 @@
 // acceptance, FindBlock and Trim).
 //  * diag_count_kernel: the diagonal histogram M[d] of Algorithm 3 (residual
 //    entries on diagonal d = j - i, |d| <= d_max), a warp per row, atomics.
-//  * fit_ribbon_kernel: FitRibbon (Section 4.2, Algorithm 3) for every row and
-//    a list of candidate offsets at once, one thread per (row, offset).
+//  * fit_ribbon_kernel: FitRibbon (Section 4.2, Algorithm 3) for every
+//    residual entry on a candidate diagonal at once (the ribbon of row i and
+//    offset d starts at the entry (i, i + d)), a warp per row.
 //  * hot_cells_kernel: the candidate-region pre-pass of the block extractor:
 //    the entries of every tile x tile cell, counted in shared memory one tile
 //    row and one column chunk at a time; cells that reach the density floor
@@ -42,30 +43,26 @@ diag_count_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci
   }
 }
 
-// ext[c * m + i] = l | u << 10 | k << 20 for offset ds[c] and row i; 0 when row
-// i has no residual entry at column i + ds[c].  zt[w] is the least numerator q
-// with q / w >= delta in FP64 (w + 1 if none), so "(z + 1) / w < delta" is
-// "z + 1 < zt[w]".  l, u <= w_max <= 512 and k <= 2 w_max + 1.
+// FitRibbon of every residual entry on a candidate diagonal: entry k of row i
+// sits at column j = i + d; when cand[d + m] is set, the ribbon of (i, d)
+// starts at that entry, so no search is needed.  ext[k] = l | u << 10 |
+// z << 20 (z = entries in the final ribbon), 0 for other entries.  zt[w] is
+// the least numerator q with q / w >= delta in FP64 (w + 1 if none), so
+// "(z + 1) / w < delta" is "z + 1 < zt[w]".  l, u <= w_max <= 512 and
+// z <= 2 w_max + 1.  A warp per row, lanes over its entries.
 __global__ void __launch_bounds__(kThreads)
-fit_ribbon_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int64_t m, int64_t n,
-                  const int64_t *__restrict__ ds, int w_max, const int32_t *__restrict__ zt,
+fit_ribbon_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int64_t m, int64_t d_max,
+                  const unsigned char *__restrict__ cand, int w_max, const int32_t *__restrict__ zt,
                   unsigned *__restrict__ ext) {
-  const int c = blockIdx.y;
-  const int64_t d = ds[c];
-  const int64_t stride = (int64_t)gridDim.x * kThreads;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < m; i += stride) {
-    unsigned out = 0;
-    const int64_t col = i + d;
-    if (col >= 0 && col < n) {
-      const int64_t b = rp[i], e = rp[i + 1];
-      int64_t lo = b, hi = e;                       // first entry with column >= col
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (ci[mid] < col) lo = mid + 1;
-        else hi = mid;
-      }
-      if (lo < e && ci[lo] == col) {
-        int64_t pl = lo, ph = lo;                   // first and last entry of the ribbon
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
+  for (int64_t i = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5; i < m; i += nw) {
+    const int64_t b = rp[i], e = rp[i + 1];
+    for (int64_t k = b + lane; k < e; k += 32) {
+      const int64_t col = ci[k], d = col - i;
+      unsigned out = 0;
+      if (d <= d_max && -d <= d_max && cand[d + m]) {
+        int64_t pl = k, ph = k;                     // first and last entry of the ribbon
         int l = 0, u = 0, z = 1;
         for (;;) {
           int wb = -1, wa = -1, nl = 0, nu = 0;
@@ -92,8 +89,8 @@ fit_ribbon_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci
         }
         out = (unsigned)l | ((unsigned)u << 10) | ((unsigned)z << 20);
       }
+      ext[k] = out;
     }
-    ext[(size_t)c * m + i] = out;
   }
 }
 
@@ -251,38 +248,34 @@ sable_status dev_diag_counts(DevResidual *D, int64_t d_max, std::vector<int64_t>
   return SABLE_OK;
 }
 
-sable_status dev_fit_ribbons(DevResidual *D, const int64_t *ds, int nd, int w_max, const std::vector<int32_t> &zt,
-                             std::vector<uint32_t> &ext) {
-  if (nd <= 0 || D->m == 0) {
-    ext.assign((size_t)std::max(nd, 0) * (size_t)D->m, 0u);
-    return SABLE_OK;
-  }
-  if (w_max < 0 || w_max > 512 || (int64_t)zt.size() < 2 * (int64_t)w_max + 2 || nd > 65535)
+sable_status dev_fit_ribbons(DevResidual *D, int64_t d_max, const std::vector<unsigned char> &cand, int w_max,
+                             const std::vector<int32_t> &zt, std::vector<uint32_t> &ext) {
+  ext.assign((size_t)D->nnz, 0u);
+  if (D->m == 0 || D->nnz == 0) return SABLE_OK;
+  if (w_max < 0 || w_max > 512 || (int64_t)zt.size() < 2 * (int64_t)w_max + 2 ||
+      (int64_t)cand.size() < D->m + D->n + 1)
     return SABLE_ERR_INVALID;
-  int64_t *dds = nullptr;
+  unsigned char *dcand = nullptr;
   int32_t *dzt = nullptr;
   unsigned *dext = nullptr;
-  const size_t cells = (size_t)nd * (size_t)D->m;
   sable_status s = alloc_fails() ? SABLE_ERR_OOM : SABLE_OK;
-  if (!s) s = cuda_status(cudaMalloc(&dds, (size_t)nd * sizeof(int64_t)));
+  if (!s) s = cuda_status(cudaMalloc(&dcand, cand.size()));
   if (!s) s = cuda_status(cudaMalloc(&dzt, zt.size() * sizeof(int32_t)));
-  if (!s) s = cuda_status(cudaMalloc(&dext, cells * sizeof(unsigned)));
-  if (!s) s = cuda_status(cudaMemcpyAsync(dds, ds, (size_t)nd * sizeof(int64_t), cudaMemcpyHostToDevice, D->st));
+  if (!s) s = cuda_status(cudaMalloc(&dext, (size_t)D->nnz * sizeof(unsigned)));
+  if (!s) s = cuda_status(cudaMemcpyAsync(dcand, cand.data(), cand.size(), cudaMemcpyHostToDevice, D->st));
   if (!s)
     s = cuda_status(cudaMemcpyAsync(dzt, zt.data(), zt.size() * sizeof(int32_t), cudaMemcpyHostToDevice, D->st));
   if (!s) {
-    const int64_t want = (D->m + kThreads - 1) / kThreads;
-    const int gx = (int)std::max<int64_t>(
-        1, std::min<int64_t>(want, std::max<int64_t>(1, (int64_t)D->sm_count * 8 / std::max(nd, 1))));
-    fit_ribbon_kernel<<<dim3(gx, nd), kThreads, 0, D->st>>>(D->rp, D->ci, D->m, D->n, dds, w_max, dzt, dext);
+    const int64_t want = (D->m + kThreads / 32 - 1) / (kThreads / 32);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)D->sm_count * 8));
+    fit_ribbon_kernel<<<grid, kThreads, 0, D->st>>>(D->rp, D->ci, D->m, d_max, dcand, w_max, dzt, dext);
     s = cuda_status(cudaGetLastError());
   }
-  if (!s) {
-    ext.resize(cells);
-    s = cuda_status(cudaMemcpyAsync(ext.data(), dext, cells * sizeof(unsigned), cudaMemcpyDeviceToHost, D->st));
-  }
+  if (!s)
+    s = cuda_status(cudaMemcpyAsync(ext.data(), dext, (size_t)D->nnz * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                    D->st));
   if (!s) s = cuda_status(cudaStreamSynchronize(D->st));
-  cudaFree(dds);
+  cudaFree(dcand);
   cudaFree(dzt);
   cudaFree(dext);
   return s;

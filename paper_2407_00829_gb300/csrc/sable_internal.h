@@ -182,10 +182,12 @@ sable_status dev_residual_open(const Csr &R, DevResidual **out);
 void dev_residual_close(DevResidual *D);
 // M[d + m] = residual entries on diagonal d, |d| <= d_max (size m + n + 1)
 sable_status dev_diag_counts(DevResidual *D, int64_t d_max, std::vector<int64_t> &M);
-// FitRibbon of every row for offsets ds[0, nd): ext[c m + i] = l | u << 10 | k << 20;
-// zt[w] = least q with q / w >= delta in FP64 (w + 1 if none), w in [0, 2 w_max + 1]
-sable_status dev_fit_ribbons(DevResidual *D, const int64_t *ds, int nd, int w_max, const std::vector<int32_t> &zt,
-                             std::vector<uint32_t> &ext);
+// FitRibbon of every residual entry (i, i + d) with |d| <= d_max and cand[d + m]
+// set: ext[k] = l | u << 10 | z << 20 for the entry at CSR position k (0 for
+// the others); zt[w] = least q with q / w >= delta in FP64 (w + 1 if none),
+// w in [0, 2 w_max + 1]
+sable_status dev_fit_ribbons(DevResidual *D, int64_t d_max, const std::vector<unsigned char> &cand, int w_max,
+                             const std::vector<int32_t> &zt, std::vector<uint32_t> &ext);
 // keys I * TJ + J of the g x g cells whose count c has c >= delta * area in FP64,
 // i.e. c >= thr[area] (area in [1, g^2]), ascending
 sable_status dev_hot_cells(DevResidual *D, int g, const std::vector<int32_t> &thr, std::vector<int64_t> &hot);

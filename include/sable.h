@@ -145,7 +145,7 @@ sable_status sable_plan_add_regions(sable_plan_t plan, sable_extractor kind, con
  * SABLE_INSPECT_HOST (default): everything on the host.  SABLE_INSPECT_DEVICE:
  * on the current CUDA device, integer arithmetic only, for each band stage the
  * diagonal histogram M[d] of Algorithm 3 and FitRibbon (Section 4.2) of every
- * row for every candidate offset, and for each block stage with tile > 0 the
+ * residual entry on a candidate diagonal, and for each block stage with tile > 0 the
  * entry counts of the candidate-region pre-pass's cells; candidate order,
  * GrowSegments (Algorithm 4), acceptance, FindBlock (Algorithm 2) and Trim
  * stay on the host.  Both give the same regions, entry for entry (each FP64

@@ -1071,8 +1071,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                          "frac": gbs / peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
                          if peak_src == "measured" else "fallback 6800 GB/s",
-                         "traffic": traffic, "kernel": "spmv_hybrid_kernel<256>",
-                         "achieved_def": "spmv_bytes per launch / mean launch time over the timed region"},
+                         "traffic": traffic, "kernel": "spmv_hybrid_kernel<false> (csrc/sable_spmv.cu)",
+                         "achieved_def": "spmv_bytes per launch / mean launch time over the timed region (K launches replayed from one CUDA graph, CUDA events on the launching stream)"},
             "pct_hbm_peak": 100.0 * gbs / peak,
             "gather_roofline": {
                 "what": "random 4-byte gathers of x by the CSR remainder, one 32-byte L2 sector each; "

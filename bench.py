@@ -304,7 +304,7 @@ def band_section(sable, torch, dev, stream, m=6_000_000):
     g = torch.cuda.CUDAGraph()
     gs = torch.cuda.Stream(dev)
     gs.wait_stream(stream)
-    with torch.cuda.graph(g, stream=gs):
+    with torch.cuda.graph(g, stream=gs, capture_error_mode="thread_local"):
         for t in range(k):
             P.spmv(xs[t % 3], ys[t % 3], gs)
     stream.wait_stream(gs)
@@ -797,7 +797,7 @@ def main():
         g = torch.cuda.CUDAGraph()
         gs = torch.cuda.Stream(dev)
         gs.wait_stream(stream)
-        with torch.cuda.graph(g, stream=gs):
+        with torch.cuda.graph(g, stream=gs, capture_error_mode="thread_local"):
             for i in range(k):
                 fn(i % reps, gs)
         stream.wait_stream(gs)

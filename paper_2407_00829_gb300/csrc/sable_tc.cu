@@ -140,7 +140,8 @@ vbr_tc_kernel(const DevHybrid *__restrict__ mats, const int32_t *__restrict__ tr
         const int n = tid;                       // one column of the tile per thread
         const bool ncol = n0 + n < N;
         const float *bp = B + (size_t)kb * ldb + n0 + n;
-#pragma unroll 2
+        // all 64 rows of the thread's column in flight at once: one load latency per K step
+#pragma unroll
         for (int k8 = 0; k8 < kTileK / 8; ++k8) {
           uint32_t w[NS][4];
 #pragma unroll

@@ -478,10 +478,23 @@ sable_status sable_error_norms(const float *y, const double *ref, int64_t count,
 
 /* The plan's device error word, 4 int32 copied to host `out` (synchronous):
  * a status recorded by a kernel (0 = none; SABLE_ERR_TIMEOUT from a bounded
- * wait of the tensor-core kernel), then three words of detail (0 unless a
- * debug build's checks recorded one).
- * Errors: SABLE_ERR_ORDER before upload; SABLE_ERR_CUDA. */
+ * wait of the tensor-core kernel; SABLE_ERR_KERNEL from an index check of the
+ * debug build), then three words of detail: for an index check, its tag (1 =
+ * SpMV CSR column, 2 = SpMV block column, 3 = SpMM CSR column, 4 = SpMM
+ * block column), the index and its bound; 0 otherwise.  The debug build is
+ * the library compiled with SABLE_CHECKS (`build.py --checks`): its SpMV and
+ * row-split SpMM kernels test every column they gather with against the
+ * matrix's width, record the first bad one here and skip it.  The word is
+ * cleared at upload.  Errors: SABLE_ERR_ORDER before upload; SABLE_ERR_CUDA. */
 sable_status sable_plan_device_error(sable_plan_t plan, int32_t *out);
+
+/* Debug build only: overwrite entry `entry` (0 .. nnz_csr - 1, in row order)
+ * of an uploaded plan's device CSR remainder columns with `value`, so that a
+ * test can make the index checks record SABLE_ERR_KERNEL.  The release build
+ * returns SABLE_ERR_UNSUPPORTED and changes nothing (its kernels do not check
+ * columns).  No counterpart in the paper.  Errors: SABLE_ERR_UNSUPPORTED;
+ * SABLE_ERR_INVALID; SABLE_ERR_ORDER before upload; SABLE_ERR_CUDA. */
+sable_status sable_debug_set_csr_column(sable_plan_t plan, int64_t entry, int32_t value);
 
 /* Testing hook, no counterpart in the paper: allocation-failure injection.
  * after >= 0 lets that many of the library's guarded allocations (plan

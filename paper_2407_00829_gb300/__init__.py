@@ -15,7 +15,9 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libsable.so")
+# the library this process loads: the release build, or another build (the
+# debug build, _build_checks/libsable.so) named by SABLE_LIB_PATH
+LIB_PATH = os.environ.get("SABLE_LIB_PATH") or os.path.join(_HERE, "_build", "libsable.so")
 
 VDIA, VBR, CSR = 0, 1, 2
 FP32, BF16_BLOCKS, FP32_SPLIT = 0, 1, 2
@@ -40,7 +42,7 @@ EXPORTED = [
     "sable_autotune_cache_clear", "sable_plan_set_spmm_cols", "sable_plan_update_values",
     "sable_plan_set_spmm_depth", "sable_plan_device_error", "sable_probe_bulk_gather", "sable_set_wait_limit",
     "sable_get_wait_limit", "sable_probe_wait_limit", "sable_debug_fail_allocations",
-    "sable_plan_set_inspector",
+    "sable_plan_set_inspector", "sable_debug_set_csr_column",
 ]
 
 NFEAT = 24
@@ -88,6 +90,7 @@ def lib():
             "sable_plan_add_extractor": ([p, i32, p], i32),
             "sable_extract": ([p], i32),
             "sable_plan_set_inspector": ([p, i32], i32),
+            "sable_debug_set_csr_column": ([p, i64, i32], i32),
             "sable_plan_upload": ([p, p], i32),
             "sable_spmv": ([p, p, p, p], i32),
             "sable_csr_spmv": ([p, p, p, p], i32),
@@ -369,10 +372,16 @@ class Plan:
         return lib().sable_plan_status(self._h)
 
     def device_error(self):
-        """[status, check, tile row, value] recorded by the plan's kernels."""
+        """[status, check tag, index, bound] recorded by the plan's kernels
+        (see sable_plan_device_error)."""
         out = (ctypes.c_int32 * 4)()
         _check(lib().sable_plan_device_error(self._h, out), "sable_plan_device_error")
         return list(out)
+
+    def debug_set_csr_column(self, entry: int, value: int):
+        """Debug build only: overwrite one device CSR remainder column."""
+        _check(lib().sable_debug_set_csr_column(self._h, int(entry), int(value)), "sable_debug_set_csr_column")
+        return self
 
     def tiling(self) -> dict:
         t = Tiling()

@@ -13,6 +13,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsable.so")
+# the debug build: the same sources with SABLE_CHECKS (index checks in the hot
+# kernels that record a bad column in the plan's device error word)
+OUT_CHECKS = os.path.join(HERE, "_build_checks")
+LIB_CHECKS = os.path.join(OUT_CHECKS, "libsable.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,28 +40,32 @@ def sources():
     return cu, cpp, hdr
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     cu, cpp, hdr = sources()
     deps = [os.path.join(SRC, f) for f in cu + cpp + hdr] + [os.path.join(INCLUDE, "sable.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
+    """Build libsable.so (checks=True: the debug build with index checks, in
+    _build_checks/) if any source is newer; returns its path."""
+    out, lib = (OUT_CHECKS, LIB_CHECKS) if checks else (OUT, LIB)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
     cu, cpp, _ = sources()
+    extra = ["-DSABLE_CHECKS"] if checks else []
     jobs = []
     for f in cu:
-        o = os.path.join(OUT, f + ".o")
-        jobs.append(([nvcc] + NVCC_FLAGS + ["-c", os.path.join(SRC, f), "-o", o], o))
+        o = os.path.join(out, f + ".o")
+        jobs.append(([nvcc] + NVCC_FLAGS + extra + ["-c", os.path.join(SRC, f), "-o", o], o))
     for f in cpp:
-        o = os.path.join(OUT, f + ".o")
-        jobs.append((["g++"] + CXX_FLAGS + ["-c", os.path.join(SRC, f), "-o", o], o))
+        o = os.path.join(out, f + ".o")
+        jobs.append((["g++"] + CXX_FLAGS + extra + ["-c", os.path.join(SRC, f), "-o", o], o))
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -68,11 +76,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
         list(ex.map(run, [j[0] for j in jobs]))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     run([nvcc] + ARCH + ["-shared", "-o", tmp] + [j[1] for j in jobs] + ["-lpthread"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checks="--checks" in sys.argv))

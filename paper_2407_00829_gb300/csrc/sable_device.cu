@@ -17,6 +17,7 @@
 #include <cstring>
 #include <new>
 
+#include "sable_checks.cuh"
 #include "sable_internal.h"
 
 using namespace sable;
@@ -164,6 +165,10 @@ __device__ __forceinline__ void row_parts(const DevHybrid &A, int r, const float
       if (k < k1) {
         v = __ldg(vp + (int64_t)k * stride);
         c = cb + k;
+        if (!index_ok(A.err, kCheckSpmmBlock, c, n)) {   // debug build: contributes nothing
+          c = 0;
+          v = 0.f;
+        }
       }
       rows_chunk<V, L, U>(acc, v, c, min(L, k1 - kb), Bl, ldb, lane_ok, mask);
     }
@@ -182,6 +187,10 @@ __device__ __forceinline__ void row_csr(const DevHybrid &A, int r, const float *
     if (p < p1) {
       v = __ldcs(A.cv + p);
       c = __ldcs(A.ci + p);
+      if (!index_ok(A.err, kCheckSpmmCsr, c, A.n)) {   // debug build: contributes nothing
+        c = 0;
+        v = 0.f;
+      }
     }
     rows_chunk<V, L, U>(acc, v, c, min(L, p1 - base), Bl, ldb, lane_ok, mask);
   }
@@ -895,6 +904,26 @@ sable_status sable_plan_update_values(sable_plan_t P, const float *val, void *st
     if (e == cudaSuccess && pt.bytes) e = cudaMemcpyAsync(blob + pt.off, pt.src, pt.bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the staging vectors die here
   return e == cudaSuccess ? SABLE_OK : cuda_fail(P, e);
+}
+
+sable_status sable_debug_set_csr_column(sable_plan_t P, int64_t entry, int32_t value) {
+#ifndef SABLE_CHECKS
+  (void)P;
+  (void)entry;
+  (void)value;
+  return SABLE_ERR_UNSUPPORTED;   // only the checked build may hold a column outside the matrix
+#else
+  if (!P) return SABLE_ERR_INVALID;
+  if (!P->uploaded) return SABLE_ERR_ORDER;
+  if (entry < 0 || entry >= P->stats.nnz_csr) return SABLE_ERR_INVALID;
+  const cudaError_t e =
+      cudaMemcpy(const_cast<int32_t *>(P->dev.ci) + entry, &value, sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SABLE_ERR_CUDA;
+  }
+  return SABLE_OK;
+#endif
 }
 
 sable_status sable_plan_device_error(sable_plan_t P, int32_t *out) {

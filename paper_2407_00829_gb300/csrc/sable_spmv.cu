@@ -24,6 +24,7 @@
 
 #include <algorithm>
 
+#include "sable_checks.cuh"
 #include "sable_internal.h"
 
 namespace sable {
@@ -115,7 +116,9 @@ __device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T,
           const float *bp = A.vbr + b.val_off + (rr - b.r0);
           const float *xp = x + b.c0;
           float acc = 0.f;
-          for (int c = warp; c < b.nc; c += NW) acc = fmaf(__ldg(bp + (size_t)c * b.nr), __ldg(xp + c), acc);
+          for (int c = warp; c < b.nc; c += NW)
+            if (index_ok(A.err, kCheckSpmvBlock, (long long)b.c0 + c, n))
+              acc = fmaf(__ldg(bp + (size_t)c * b.nr), __ldg(xp + c), acc);
           atomicAdd(&ys[rr - r0], acc);
         }
       }
@@ -137,8 +140,14 @@ __device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T,
           else hi = mid;
         }
         int cur = lo, nxt = rps[lo + 1], cnt = 0;
-        const float vv[4] = {v.x, v.y, v.z, v.w};
-        const int cc[4] = {c.x, c.y, c.z, c.w};
+        float vv[4] = {v.x, v.y, v.z, v.w};
+        int cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)   // debug build: a column outside the matrix contributes nothing
+          if (p0 + e >= pb && p0 + e < pe && !index_ok(A.err, kCheckSpmvCsr, cc[e], n)) {
+            cc[e] = 0;
+            vv[e] = 0.f;
+          }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int pp = p0 + e;

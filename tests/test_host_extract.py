@@ -331,3 +331,15 @@ def test_device_inspector_without_a_gpu_reports_cuda_error():
     P.add_extractor(sable.VBR, tile=0).add_extractor(sable.CSR).set_inspector(sable.INSPECT_DEVICE).extract()
     assert P.info()["nnz"] == A["row"].size
     P.close()
+
+
+def test_release_build_refuses_the_debug_column_hook():
+    """The hook that writes a column outside the matrix exists only in the
+    debug build: the release library answers SABLE_ERR_UNSUPPORTED before
+    looking at its arguments (no GPU needed)."""
+    L = sable.lib()
+    A = synth.assemble(np.random.default_rng(4), 64, 64, n_scatter=200)
+    P = sable.plan_from(A, [(sable.CSR, None)], upload=False)
+    assert L.sable_debug_set_csr_column(P.handle, 0, 1000) == 8
+    assert L.sable_debug_set_csr_column(None, 0, 0) == 8
+    P.close()

@@ -63,9 +63,10 @@ def build(force: bool = False, verbose: bool = False, checks: bool = False) -> s
     for f in cu:
         o = os.path.join(out, f + ".o")
         jobs.append(([nvcc] + NVCC_FLAGS + extra + ["-c", os.path.join(SRC, f), "-o", o], o))
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")   # NVTX header
     for f in cpp:
         o = os.path.join(out, f + ".o")
-        jobs.append((["g++"] + CXX_FLAGS + extra + ["-c", os.path.join(SRC, f), "-o", o], o))
+        jobs.append((["g++"] + CXX_FLAGS + extra + [f"-I{cuda_inc}", "-c", os.path.join(SRC, f), "-o", o], o))
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -13,6 +13,7 @@
 #include <stdexcept>
 
 #include "sable_internal.h"
+#include "sable_trace.h"
 
 using namespace sable;
 
@@ -305,6 +306,7 @@ struct DevStage {
 }  // namespace
 
 sable_status sable_extract(sable_plan_t P) {
+  sable::TraceRange trace_("sable_extract");
   if (!P) return SABLE_ERR_INVALID;
   if (P->sticky) return P->sticky;
   if (P->extracted) return SABLE_ERR_ORDER;

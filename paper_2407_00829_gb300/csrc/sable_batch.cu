@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "sable_internal.h"
+#include "sable_trace.h"
 
 using namespace sable;
 
@@ -102,6 +103,7 @@ sable_status capture(sable_batch_t b, sable_graph_t *out, bool spmm, const float
 extern "C" {
 
 sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_batch_t *out) {
+  sable::TraceRange trace_("sable_batch_create");
   if (!out || count < 0 || (count > 0 && !plans)) return SABLE_ERR_INVALID;
   *out = nullptr;
   int dev = -1;
@@ -192,12 +194,14 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
 }
 
 sable_status sable_batch_spmv(sable_batch_t b, const float *const *x, float *const *y, void *stream) {
+  sable::TraceRange trace_("sable_batch_spmv");
   if (!b || (b->n_v > 0 && (!x || !y))) return SABLE_ERR_INVALID;
   return batch_spmv_launch(b, x, y, (cudaStream_t)stream);
 }
 
 sable_status sable_batch_spmm(sable_batch_t b, const float *const *B, int64_t N, float *const *C,
                               sable_precision prec, void *stream) {
+  sable::TraceRange trace_("sable_batch_spmm");
   if (!b || (b->rows > 0 && (!B || !C))) return SABLE_ERR_INVALID;
   return batch_spmm_launch(b, B, N, C, prec, (cudaStream_t)stream);
 }
@@ -214,6 +218,7 @@ sable_status sable_batch_graph_spmm(sable_batch_t b, const float *const *B, int6
 }
 
 sable_status sable_graph_launch(sable_graph_t g, void *stream) {
+  sable::TraceRange trace_("sable_graph_launch");
   if (!g || !g->exec) return SABLE_ERR_INVALID;
   return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? SABLE_OK : SABLE_ERR_CUDA;
 }

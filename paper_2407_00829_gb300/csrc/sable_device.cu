@@ -19,6 +19,7 @@
 
 #include "sable_checks.cuh"
 #include "sable_internal.h"
+#include "sable_trace.h"
 
 using namespace sable;
 
@@ -482,6 +483,7 @@ static sable_status cuda_fail(sable_plan_t P, cudaError_t e) {
 extern "C" {
 
 sable_status sable_plan_upload(sable_plan_t P, void *stream) {
+  sable::TraceRange trace_("sable_plan_upload");
   if (!P) return SABLE_ERR_INVALID;
   if (P->sticky) return P->sticky;
   if (!P->extracted) return SABLE_ERR_ORDER;
@@ -807,12 +809,14 @@ sable_status launch_spmm(sable_plan_t P, const DevHybrid &D, const float *B, int
 extern "C" {
 
 sable_status sable_spmv(sable_plan_t P, const float *x, float *y, void *stream) {
+  sable::TraceRange trace_("sable_spmv");
   const sable_status s = check_ready(P);
   if (s) return s;
   return launch_spmv(P, P->dev, false, x, y, (cudaStream_t)stream);
 }
 
 sable_status sable_csr_spmv(sable_plan_t P, const float *x, float *y, void *stream) {
+  sable::TraceRange trace_("sable_csr_spmv");
   const sable_status s = check_ready(P);
   if (s) return s;
   return launch_spmv(P, P->dev_plain, true, x, y, (cudaStream_t)stream);
@@ -820,6 +824,7 @@ sable_status sable_csr_spmv(sable_plan_t P, const float *x, float *y, void *stre
 
 sable_status sable_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, float *C, int64_t ldc,
                         sable_precision prec, void *stream) {
+  sable::TraceRange trace_("sable_spmm");
   const sable_status s = check_ready(P);
   if (s) return s;
   if (prec != SABLE_FP32 && prec != SABLE_BF16_BLOCKS && prec != SABLE_FP32_SPLIT) return SABLE_ERR_INVALID;
@@ -842,6 +847,7 @@ sable_status sable_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, 
 
 sable_status sable_csr_spmm(sable_plan_t P, const float *B, int64_t N, int64_t ldb, float *C, int64_t ldc,
                             void *stream) {
+  sable::TraceRange trace_("sable_csr_spmm");
   const sable_status s = check_ready(P);
   if (s) return s;
   return launch_spmm(P, P->dev_plain, B, N, ldb, C, ldc, false, (cudaStream_t)stream);

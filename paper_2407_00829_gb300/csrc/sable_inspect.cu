@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "sable_internal.h"
+#include "sable_trace.h"
 
 namespace sable {
 
@@ -225,6 +226,7 @@ sable_status dev_residual_open(const Csr &R, DevResidual **out) {
 }
 
 sable_status dev_diag_counts(DevResidual *D, int64_t d_max, std::vector<int64_t> &M) {
+  sable::TraceRange trace_("inspect_diag_counts");
   const int64_t span = D->m + D->n;
   unsigned *dM = nullptr;
   sable_status s = alloc_fails() ? SABLE_ERR_OOM : SABLE_OK;
@@ -250,6 +252,7 @@ sable_status dev_diag_counts(DevResidual *D, int64_t d_max, std::vector<int64_t>
 
 sable_status dev_fit_ribbons(DevResidual *D, int64_t d_max, const std::vector<unsigned char> &cand, int w_max,
                              const std::vector<int32_t> &zt, std::vector<uint32_t> &ext) {
+  sable::TraceRange trace_("inspect_fit_ribbons");
   ext.assign((size_t)D->nnz, 0u);
   if (D->m == 0 || D->nnz == 0) return SABLE_OK;
   if (w_max < 0 || w_max > 512 || (int64_t)zt.size() < 2 * (int64_t)w_max + 2 ||
@@ -282,6 +285,7 @@ sable_status dev_fit_ribbons(DevResidual *D, int64_t d_max, const std::vector<un
 }
 
 sable_status dev_hot_cells(DevResidual *D, int g, const std::vector<int32_t> &thr, std::vector<int64_t> &hot) {
+  sable::TraceRange trace_("inspect_hot_cells");
   hot.clear();
   if (g < 1 || g > 64 || (int64_t)thr.size() < (int64_t)g * g + 1) return SABLE_ERR_INVALID;
   if (D->m == 0 || D->n == 0 || D->nnz == 0) return SABLE_OK;

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "sable_internal.h"
+#include "sable_trace.h"
 
 namespace sable {
 namespace {
@@ -132,6 +133,7 @@ sable_status sable_plan_get_tiling(sable_plan_t P, sable_tiling *out) {
 
 sable_status sable_autotune(sable_plan_t P, int32_t op, int64_t N, const float *in, float *out, int32_t reps,
                             int32_t use_cache, sable_tiling *chosen, float *chosen_ms, void *stream) {
+  sable::TraceRange trace_("sable_autotune");
   const bool spmv = op == 0 || op == 4;
   if (!P || op < 0 || op > 4 || (!spmv && N < 1) || !in || !out || reps < 1 || reps > 10000)
     return SABLE_ERR_INVALID;

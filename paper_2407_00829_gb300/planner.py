@@ -383,7 +383,10 @@ def main():
     ap.add_argument("--test", type=int, default=200)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--weights", default=None)
+    ap.add_argument("--rows-max", type=int, default=1_000_000,
+                    help="matrices' rows drawn log-uniform in [100k, rows-max] (regions and collect alike)")
     a = ap.parse_args()
+    rows = (100_000, a.rows_max)
     if a.cmd == "regions":
         import synth
         os.makedirs(a.out, exist_ok=True)
@@ -392,7 +395,7 @@ def main():
             if os.path.exists(path):
                 continue
             t0 = time.perf_counter()
-            A = synth.planner_set_matrix(i, seed=a.seed)
+            A = synth.planner_set_matrix(i, seed=a.seed, rows=rows)
             save_matrix_tables(path + ".tmp.npz", A, region_tables(A))
             os.replace(path + ".tmp.npz", path)
             print(f"{i} m={A['m']} nnz={A['row'].size} {time.perf_counter() - t0:.1f}s", flush=True)
@@ -400,7 +403,8 @@ def main():
     import torch
     torch.cuda.set_device(0)
     if a.cmd == "collect":
-        d = collect(range(a.start, a.stop), seed=a.seed, table_dir=a.tables, log=lambda s: print(s, flush=True))
+        d = collect(range(a.start, a.stop), seed=a.seed, rows=rows, table_dir=a.tables,
+                    log=lambda s: print(s, flush=True))
         np.savez_compressed(a.out, **d)
     else:
         parts = [dict(np.load(p)) for p in a.data]

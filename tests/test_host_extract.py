@@ -343,3 +343,15 @@ def test_release_build_refuses_the_debug_column_hook():
     assert L.sable_debug_set_csr_column(P.handle, 0, 1000) == 8
     assert L.sable_debug_set_csr_column(None, 0, 0) == 8
     P.close()
+
+
+def test_debug_build_compiles_and_exports_the_same_symbols():
+    """The debug build (index checks in the hot kernels) builds from the same
+    sources and exports every declared entry point, like the release build."""
+    import ctypes
+    from paper_2407_00829_gb300 import build
+    lib = build.build(checks=True)
+    L = ctypes.CDLL(lib)
+    hdr = open(os.path.join(ROOT, "include", "sable.h")).read()
+    declared = set(re.findall(r"\b(sable_[a-z0-9_]+)\s*\(", hdr))
+    assert [d for d in sorted(declared) if not hasattr(L, d)] == []

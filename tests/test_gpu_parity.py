@@ -214,3 +214,41 @@ def test_blocks_scatter_200k_full_size_sampled():
             torch.cuda.synchronize()
             assert oracle.normwise_err(C[torch.from_numpy(sel).cuda()].cpu().numpy(), ref) <= tol
     P.close()
+
+
+def test_single_plan_calls_replay_from_a_cuda_graph():
+    """SpMV (hybrid and plain CSR) and SpMM (FP32 blocks) of one plan captured
+    in a CUDA graph on a side stream and replayed twice, with new x / B
+    values copied in between: every replay matches the oracle."""
+    A = synth.blocks_bands_scatter_4096()
+    P = sable.plan_from(A, ALL3)
+    m, n, N = A["m"], A["n"], 64
+    x = torch.empty(n, device="cuda")
+    y = torch.empty(m, device="cuda")
+    yp = torch.empty(m, device="cuda")
+    B = torch.empty(n, N, device="cuda")
+    C = torch.empty(m, N, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+        P.spmv(x, y, side)
+        P.csr_spmv(x, yp, side)
+        P.spmm(B, C, sable.FP32, side)
+    for seed in (21, 22):
+        xs = synth.dense_operand(seed, n)
+        Bs = synth.dense_operand(seed + 100, n, N)
+        x.copy_(_dev(xs))
+        B.copy_(_dev(Bs))
+        y.fill_(float("nan"))
+        yp.fill_(float("nan"))
+        C.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        ref = oracle.spmv(m, A["row"], A["col"], A["val"], xs)
+        assert oracle.normwise_err(y.cpu().numpy(), ref) <= TOL_FP32
+        assert oracle.normwise_err(yp.cpu().numpy(), ref) <= TOL_FP32
+        refC = oracle.spmm(m, A["row"], A["col"], A["val"], Bs)
+        assert oracle.normwise_err(C.cpu().numpy(), refC) <= TOL_FP32
+    del g
+    P.close()

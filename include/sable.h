@@ -174,7 +174,13 @@ sable_status sable_extract(sable_plan_t plan);
  * before sable_extract; SABLE_ERR_OOM / SABLE_ERR_CUDA. */
 sable_status sable_plan_upload(sable_plan_t plan, void *stream);
 
-/* y := A x.  x: device, n floats; y: device, m floats (overwritten).
+/* y := A x.  x: device, n floats; y: device, m floats (overwritten).  One
+ * launch over the plan's row tiles; when the upload cut a tile whose CSR range
+ * is longer than two chunks (rows of tens of thousands of entries; a chunk is
+ * the entries of one tile at the byte target, at least 4096), partial tiles
+ * sum the rest of that range on other CTAs and a second, small launch adds
+ * their row sums to y.  Those partial sums live in the plan's device memory:
+ * two SpMVs of such a plan must not run at the same time (on two streams).
  * Errors: SABLE_ERR_ORDER before upload; SABLE_ERR_INVALID; SABLE_ERR_CUDA. */
 sable_status sable_spmv(sable_plan_t plan, const float *x, float *y, void *stream);
 
@@ -308,7 +314,9 @@ int64_t sable_autotune_cache_clear(void);
  * outlive the batch).  It concatenates their row-tile tables, each tile
  * tagged with its matrix, so that one launch computes every region of every
  * matrix.  Errors: SABLE_ERR_ORDER if a plan is not uploaded;
- * SABLE_ERR_INVALID (NULL, other device, plan in error); SABLE_ERR_OOM. */
+ * SABLE_ERR_INVALID (NULL, other device, plan in error); SABLE_ERR_OOM;
+ * SABLE_ERR_UNSUPPORTED for a plan whose SpMV tiles were cut (a CSR range of
+ * more than two chunks, see sable_spmv): run such a plan on its own. */
 sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_batch_t *out);
 
 /* y_i := A_i x_i for every matrix i of the batch, one launch.  x and y are

@@ -121,6 +121,10 @@ sable_status sable_batch_create(const sable_plan_t *plans, int32_t count, sable_
         delete b;
         return P && !P->uploaded ? SABLE_ERR_ORDER : SABLE_ERR_INVALID;
       }
+      if (P->dev.spmv.n_fix > 0) {   // cut tiles need their own second launch per plan
+        delete b;
+        return SABLE_ERR_UNSUPPORTED;
+      }
       b->plans.push_back(P);
       mats.push_back(P->dev);
       for (DevItem it : P->h_items_v) {

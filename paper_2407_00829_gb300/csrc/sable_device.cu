@@ -373,11 +373,21 @@ struct HostItems {
   std::vector<DevSeg> pseg;
   std::vector<DevBlk> pblk;
   int32_t rows_max = 0;
+  std::vector<int32_t> fix;   // 4 per cut tile: first row, rows, first part slot, partial tiles
+  int64_t n_slots = 0;        // partial row sums
 };
+
+// A tile's CSR range longer than two chunks (a few long rows) is cut: the tile
+// keeps its first chunk, partial tiles take the rest; a chunk is the entries a
+// tile of the byte target holds, at least this many.
+constexpr int64_t kSplitMinEntries = 4096;
 
 // Cut rows into SpMV tiles of at most rows_max rows (multiples of 4) whose
 // summed per-row algorithmic bytes stay near `target`; list the
-// segments/blocks touching each.
+// segments/blocks touching each.  A tile of one 4-row group whose CSR range
+// exceeds two chunks (rows of tens of thousands of entries) keeps its first
+// chunk and hands the rest to partial tiles of one chunk each, run by other
+// CTAs; their row sums are added to y by a second launch.
 static HostItems build_items(int64_t m, const std::vector<Segment> &segs,
                              const std::vector<Block> &blks, const std::vector<int64_t> &rp,
                              int rows_max, int64_t target) {
@@ -436,7 +446,29 @@ static HostItems build_items(int64_t m, const std::vector<Segment> &segs,
     for (int32_t q : as) vc += (std::min(b, segs[q].row0 + segs[q].nrows) - std::max(a, segs[q].row0)) * segs[q].ndiag;
     for (int32_t q : ab) vc += (std::min(b, blks[q].r0 + blks[q].nr) - std::max(a, blks[q].r0)) * blks[q].nc;
     it.vcells = (int32_t)std::min<int64_t>(vc, INT32_MAX);
-    H.items.push_back(it);
+    const int64_t chunk = std::max<int64_t>(kSplitMinEntries, target / 8);
+    if (rp[b] - rp[a] > 2 * chunk) {
+      it.pe = (int32_t)(rp[a] + chunk);
+      H.items.push_back(it);
+      const int64_t first = H.n_slots;
+      int64_t nparts = 0;
+      for (int64_t p = rp[a] + chunk; p < rp[b]; p += chunk) {
+        DevItem pt{};
+        pt.r0 = (int32_t)a;
+        pt.r1 = (int32_t)b;
+        pt.seg_lo = pt.seg_hi = (int32_t)H.iseg.size();
+        pt.blk_lo = pt.blk_hi = (int32_t)H.iblk.size();
+        pt.pb = (int32_t)p;
+        pt.pe = (int32_t)std::min<int64_t>(rp[b], p + chunk);
+        pt.part = (int32_t)(H.n_slots + 1);
+        H.n_slots += b - a;
+        H.items.push_back(pt);
+        ++nparts;
+      }
+      H.fix.insert(H.fix.end(), {(int32_t)a, (int32_t)(b - a), (int32_t)first, (int32_t)nparts});
+    } else {
+      H.items.push_back(it);
+    }
     H.rows_max = std::max<int32_t>(H.rows_max, (int32_t)(b - a));
   }
   return H;
@@ -613,7 +645,7 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
   const size_t o_pcv = ar.add(S->pcv.data(), vec_bytes(S->pcv));
   const size_t o_srp = ar.add(S->srp.data(), vec_bytes(S->srp));
   const size_t o_sref = ar.add(S->sref.data(), vec_bytes(S->sref));
-  size_t o_it[2][6];
+  size_t o_it[2][8];
   HostItems *its[2] = {&S->it_v, &S->pit_v};
   for (int k = 0; k < 2; ++k) {
     for (int32_t q : its[k]->iseg) its[k]->pseg.push_back(S->segs[q]);
@@ -623,6 +655,8 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
     o_it[k][0] = ar.add(its[k]->items.data(), vec_bytes(its[k]->items));
     o_it[k][1] = ar.add(its[k]->iseg.data(), vec_bytes(its[k]->iseg));
     o_it[k][2] = ar.add(its[k]->iblk.data(), vec_bytes(its[k]->iblk));
+    o_it[k][6] = ar.add(its[k]->fix.data(), vec_bytes(its[k]->fix));
+    o_it[k][7] = ar.reserve((size_t)its[k]->n_slots * sizeof(float));
   }
   char *blob = nullptr;
   e = alloc_fails() ? cudaErrorMemoryAllocation : cudaMalloc(&blob, ar.off);
@@ -648,6 +682,9 @@ sable_status sable_plan_upload(sable_plan_t P, void *stream) {
     d.pblk = reinterpret_cast<const DevBlk *>(blob + o_it[k][5]);
     d.n = (int32_t)h->items.size();
     d.rows_max = h->rows_max;
+    d.fix = reinterpret_cast<const int32_t *>(blob + o_it[k][6]);
+    d.n_fix = (int32_t)(h->fix.size() / 4);
+    d.part = reinterpret_cast<float *>(blob + o_it[k][7]);
     return d;
   };
   DevHybrid &D = P->dev;

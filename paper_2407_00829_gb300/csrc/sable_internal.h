@@ -59,7 +59,9 @@ struct DevItem {         // 48 bytes: one row tile of a launch
   int32_t mat;           // matrix index (batched launches), 0 otherwise
   int32_t pb, pe;        // CSR remainder entries of the rows: [pb, pe)
   int32_t vcells;        // VDIA + VBR cells of the tile's rows
-  int32_t pad[2];
+  int32_t part;          // 0: the tile stores its rows of y; k + 1: a partial tile (a long
+                         // CSR range cut in chunks) that stores its row sums in part[k ..]
+  int32_t pad;
 };
 
 // Row tiles of one launch: items, and per item the indices of the segments
@@ -72,6 +74,11 @@ struct DevItems {
   const DevBlk *pblk = nullptr;    // copies of blks[iblk[k]]
   int32_t n = 0;
   int32_t rows_max = 0;          // largest r1 - r0
+  // tiles whose CSR range was cut: (first row, rows, first part slot, partial
+  // tiles) per cut tile; a second launch adds their partial sums to y
+  const int32_t *fix = nullptr;  // 4 int32 per cut tile
+  int32_t n_fix = 0;
+  float *part = nullptr;         // partial row sums, written by the partial tiles
 };
 
 // Device copy of one hybrid matrix.

@@ -49,8 +49,10 @@ __device__ __forceinline__ int4 ld_stream_i4(const int *p) {
   return r;
 }
 
-template <bool PLAIN>
-__device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T, const DevItem &I,
+// CUT: the launch's tile table may hold partial tiles (single-plan launches;
+// a batch refuses plans with cut tiles)
+template <bool PLAIN, bool CUT>
+__device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T, const DevItem &I, int it,
                                           const float *__restrict__ x, float *__restrict__ y, float *ys,
                                           int *rps) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -58,7 +60,10 @@ __device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T,
   const unsigned n = (unsigned)A.n;
   {
     const int r0 = I.r0, R = I.r1 - I.r0;
-    for (int i = tid; i <= R; i += kThreads) rps[i] = __ldg(A.rp + r0 + i);
+    // row pointers clamped to the tile's CSR range: a no-op for a whole tile;
+    // for a cut tile (its first chunk, or a partial tile) only the chunk's
+    // entries remain, each in its own row
+    for (int i = tid; i <= R; i += kThreads) rps[i] = min(max(__ldg(A.rp + r0 + i), I.pb), I.pe);
 
     // ---- A. VDIA: a quad of 4 consecutive rows; when the tile has fewer
     // quads than threads, S threads (adjacent lanes) split the quad's
@@ -175,7 +180,11 @@ __device__ __forceinline__ void spmv_tile(const DevHybrid &A, const DevItems &T,
       if (row >= 0 && (lane == 31 || rn != row)) atomicAdd(&ys[row], run);
     }
     __syncthreads();
-    for (int i = tid; i < R; i += kThreads) y[r0 + i] = ys[i];
+    const int part = CUT ? __ldg(&T.items[it].part) : 0;   // read again here, not held through the phases
+    if (part == 0)
+      for (int i = tid; i < R; i += kThreads) y[r0 + i] = ys[i];
+    else   // a partial tile: its row sums go to the part slots, added to y by spmv_fixup_kernel
+      for (int i = tid; i < R; i += kThreads) T.part[part - 1 + i] = ys[i];
     __syncthreads();
   }
 }
@@ -189,7 +198,7 @@ spmv_hybrid_kernel(const __grid_constant__ DevHybrid A, const float *__restrict_
   int *rps = reinterpret_cast<int *>(ys + A.spmv.rows_max);
   for (int it = blockIdx.x; it < A.spmv.n; it += gridDim.x) {
     const DevItem I = A.spmv.items[it];
-    spmv_tile<PLAIN>(A, A.spmv, I, x, y, ys, rps);
+    spmv_tile<PLAIN, true>(A, A.spmv, I, it, x, y, ys, rps);
   }
 }
 
@@ -204,7 +213,25 @@ spmv_grouped_kernel(const DevHybrid *__restrict__ mats, const DevItem *__restric
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const DevItem I = items[it];
     const DevHybrid &A = mats[I.mat];
-    spmv_tile<false>(A, A.spmv, I, xs[I.mat], yv[I.mat], ys, rps);
+    spmv_tile<false, false>(A, A.spmv, I, it, xs[I.mat], yv[I.mat], ys, rps);
+  }
+}
+
+// y[r] += the partial row sums of the cut tiles, in partial-tile order: a warp
+// per cut tile, lanes over its rows.  Runs after spmv_hybrid_kernel on the
+// same stream (the owning tiles have stored their rows by then).
+__global__ void __launch_bounds__(kThreads)
+spmv_fixup_kernel(const int32_t *__restrict__ fix, int n_fix, const float *__restrict__ part,
+                  float *__restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (kThreads / 32);
+  for (int f = (blockIdx.x * kThreads + threadIdx.x) >> 5; f < n_fix; f += nw) {
+    const int r0 = fix[4 * f], R = fix[4 * f + 1], first = fix[4 * f + 2], np = fix[4 * f + 3];
+    for (int i = lane; i < R; i += 32) {
+      float acc = 0.f;
+      for (int k = 0; k < np; ++k) acc += part[first + k * R + i];
+      y[r0 + i] += acc;
+    }
   }
 }
 
@@ -239,6 +266,10 @@ sable_status launch_spmv(sable_plan_t P, const DevHybrid &D, bool plain, const f
   }
   const int grid = std::max(1, std::min(D.spmv.n, per_sm * std::max(P->sm_count, 1)));
   k<<<grid, kThreads, smem, st>>>(D, x, y);
+  if (D.spmv.n_fix > 0) {
+    const int fgrid = std::max(1, std::min((D.spmv.n_fix + kThreads / 32 - 1) / (kThreads / 32), 4 * P->sm_count));
+    spmv_fixup_kernel<<<fgrid, kThreads, 0, st>>>(D.spmv.fix, D.spmv.n_fix, D.spmv.part, y);
+  }
   if (cudaGetLastError() != cudaSuccess) {
     (void)cudaGetLastError();
     return fail(P, SABLE_ERR_CUDA);

@@ -252,3 +252,51 @@ def test_single_plan_calls_replay_from_a_cuda_graph():
         assert oracle.normwise_err(C.cpu().numpy(), refC) <= TOL_FP32
     del g
     P.close()
+
+
+def test_long_rows_cut_across_tiles():
+    """Rows of 150,000 entries (two in one 4-row group, one alone) among short
+    rows: their tiles' CSR ranges are cut into chunks summed by other CTAs,
+    and a second launch adds the partial sums.  Hybrid and plain CSR SpMV
+    match the oracle on repeated calls and under CUDA-graph replay; a batch
+    refuses the plan (its grouped launch has no second launch)."""
+    rng = np.random.default_rng(61)
+    m = n = 200_000
+    long_rows = (10, 11, 50_003)
+    R = [rng.integers(0, m, 1_000_000)]
+    C = [rng.integers(0, n, 1_000_000)]
+    for r in long_rows:
+        cols = rng.choice(n, 150_000, replace=False)
+        R.append(np.full(cols.size, r))
+        C.append(cols)
+    i = np.arange(m)
+    R.append(i)
+    C.append(i)
+    row = np.concatenate(R)
+    col = np.concatenate(C)
+    key = np.unique(row * n + col)
+    A = dict(m=m, n=n, row=(key // n).astype(np.int32), col=(key % n).astype(np.int32),
+             val=rng.uniform(-1, 1, key.size).astype(np.float32))
+    P = sable.plan_from(A, [(sable.VDIA, None), (sable.CSR, None)])
+    x = synth.dense_operand(62, n)
+    ref = oracle.spmv(m, A["row"], A["col"], A["val"], x)
+    for _ in range(3):
+        assert oracle.normwise_err(_spmv(P, x), ref) <= TOL_FP32
+        assert oracle.normwise_err(_spmv(P, x, plain=True), ref) <= TOL_FP32
+    xd = _dev(x)
+    y = torch.empty(m, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+        P.spmv(xd, y, side)
+    for _ in range(2):
+        y.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert oracle.normwise_err(y.cpu().numpy(), ref) <= TOL_FP32
+    del g
+    with pytest.raises(sable.SableError) as e:
+        sable.Batch([P])
+    assert e.value.status == 8
+    P.close()
